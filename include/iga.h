@@ -1,0 +1,238 @@
+/*
+ * iga.h - C ABI of the GB300 (sm_103a) surrogate-matrix IGA wave library.
+ *
+ * The library implements the data-parallel hot path of the surrogate matrix
+ * methodology for isogeometric analysis of waves (Drzisga, Keith, Wohlmuth,
+ * arXiv:2004.05197):
+ *   (a) Gauss quadrature of the true stiffness / mass rows at a sparse lattice
+ *       of sample rows and on the boundary band (Sec. 3.2-3.4, Sec. 5.1),
+ *   (b) degree-q B-spline interpolation of every stencil function and
+ *       evaluation of the surrogate stencils of every row (Sec. 3.3, Sec. 5.1,
+ *       Eq. DefinitionOfSurrogateMatrixSymmetric, ..SymmetricKernel),
+ *   (c) matrix-free application of the surrogate operators, Jacobi-PCG on the
+ *       consistent surrogate mass and leapfrog time stepping (Sec. 3.3: stored
+ *       stencil-function data read during every matrix-vector product).
+ *
+ * Conventions (every entry point):
+ *   - returns int: IGA_OK (0) or a negative IGA_ERR_* code; iga_last_error()
+ *     returns a thread-local message for the last failure.  No C++ exception
+ *     crosses the ABI.
+ *   - handles (iga_space, iga_ops, iga_wave) are opaque and owned by the
+ *     library; free them with the matching *_destroy.  A handle must outlive
+ *     all stream work that uses it.
+ *   - "device pointer" arguments are borrowed CUDA device memory of the
+ *     current device; the library never frees them and the caller keeps them
+ *     alive until the stream work completes.  "host pointer" arguments are
+ *     read (or written) before the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream), owned by the caller.  Calls are asynchronous on that stream
+ *     unless they return host data (documented per call).
+ *   - Vectors over the basis are stored [nrhs][N] contiguous, global index in
+ *     colexicographic order i = i_1 + i_2 m + i_3 m^2 (0-based; Sec. 3.1).
+ *   - Stencil offsets delta in {-p..p}^d are enumerated colexicographically,
+ *     t = sum_k (delta_k + p) (2p+1)^k; t0 = ((2p+1)^d - 1)/2 is delta = 0 and
+ *     t > t0 exactly when the linear offset Delta = delta_1 + delta_2 m + ... > 0.
+ *   - Stencil fields (structure-of-arrays, row pitch `pitch` >= N):
+ *       K~ field f (0 <= f < nK = t0):    F_K[f][i] = K~(i, i + Delta_{t0+1+f})
+ *       M~ field f (0 <= f < nM = t0+1): F_M[f][i] = M~(i, i + Delta_{t0+f})
+ *     (upper triangle of the symmetric matrices; 0 where the column leaves
+ *     the index grid).  The K~ diagonal is not stored: by
+ *     Eq. DefinitionOfSurrogateMatrixSymmetricKernel it is minus the
+ *     off-diagonal row sum, and the K~ apply uses the difference form
+ *     (K~x)_i = sum_{j != i} K~_ij (x_j - x_i).
+ */
+#ifndef IGA_H
+#define IGA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define IGA_OK                  0
+#define IGA_ERR_ARG            -1   /* invalid argument or unsupported configuration */
+#define IGA_ERR_OOM            -2   /* device or host allocation failed */
+#define IGA_ERR_CUDA           -3   /* a CUDA runtime call failed */
+#define IGA_ERR_NOT_CONVERGED  -4   /* CG reached max_it before rtol for some RHS */
+#define IGA_ERR_NONFINITE      -5   /* a NaN / Inf was detected on the device */
+#define IGA_ERR_TIMEOUT        -6   /* a bounded device-side wait gave up */
+
+/* ---- enumerations ---------------------------------------------------- */
+#define IGA_MAP_IDENTITY         0  /* F(s) = s */
+#define IGA_MAP_ANNULUS_QUARTER  1  /* F(s,t) = ((1+s) cos(pi t/2), (1+s) sin(pi t/2)) */
+#define IGA_MAP_CUBE_SINE        2  /* x_k = s_k + a sin(pi s) sin(pi t) sin(pi u), a = map_param */
+
+#define IGA_COEF_CONST    0  /* c = coef_param */
+#define IGA_COEF_SINCOS   1  /* c(x) = 1 + coef_param sin(2 pi x_1) cos(2 pi x_2), x = F(s) physical */
+#define IGA_COEF_BSPLINE  2  /* c(s) = sum_k theta_k B_k(s), open uniform knots on [0,1]^d */
+
+#define IGA_F32 0   /* FP32 stencil fields and vectors, FP64 reductions */
+#define IGA_F64 1   /* FP64 everywhere */
+
+#define IGA_OP_K 0  /* surrogate stiffness K~ */
+#define IGA_OP_M 1  /* surrogate mass M~ */
+
+/* surrogate_assemble flags */
+#define IGA_TRUE_ONLY     1u  /* full quadrature of every entry: the true K, M (no surrogate) */
+#define IGA_KEEP_SAMPLES  2u  /* keep sample tables and interpolation coefficients for export */
+
+/* mass_solve flags */
+#define IGA_SOLVE_PLAIN   1u  /* non-persistent schedule: one launch per CG phase, host-side
+                                 convergence test every iteration (reference schedule) */
+
+/* wave initial conditions */
+#define IGA_INIT_ZERO         0
+#define IGA_INIT_GAUSS_PULSE  1  /* u0_i = exp(-|F(gamma_i) - F(s_c)|^2 / (2 w^2)), Greville gamma */
+
+typedef struct iga_space iga_space;
+typedef struct iga_ops iga_ops;
+typedef struct iga_wave iga_wave;
+
+/* ---- space ------------------------------------------------------------
+ * Tensor-product B-spline space of degree p on open uniform knots with n_el
+ * elements in every direction (Sec. 3.1: m = n_el + p functions per direction,
+ * h = 1/(m-p)), the geometry map and the wave-speed coefficient c (stiffness
+ * weight c^2, Eq. LinearWaveEnergy).
+ */
+typedef struct iga_space_desc {
+    int dim;               /* 2 or 3 */
+    int p;                 /* spline degree, 1..3 */
+    int n_el;              /* elements per direction, >= 4p+2 */
+    int map_kind;          /* IGA_MAP_* (ANNULUS_QUARTER needs dim 2, CUBE_SINE dim 3) */
+    double map_param;      /* CUBE_SINE amplitude */
+    int coef_kind;         /* IGA_COEF_* */
+    double coef_param;     /* CONST: c; SINCOS: amplitude */
+    const double* theta;   /* host pointer, BSPLINE: n_theta^dim coefficients, colex; copied */
+    int n_theta;           /* BSPLINE: coefficients per direction (> theta_degree) */
+    int theta_degree;      /* BSPLINE: degree of the coefficient spline, 1..5 */
+    int quad_pts;          /* Gauss points per direction and element; 0 => p+1 (Sec. 5.1); <= 8 */
+} iga_space_desc;
+
+typedef struct iga_space_info {
+    int dim, p, n_el, m;
+    long long N;           /* m^dim */
+    int D;                 /* (2p+1)^dim stencil offsets (Sec. 3.2) */
+    int nK, nM;            /* stored K~ / M~ fields: (D-1)/2 and (D+1)/2 */
+    int interior_lo, interior_hi;  /* 0-based Omega~ index range per direction: [2p, m-2p-1] */
+} iga_space_info;
+
+/* Validates desc, uploads the quadrature / basis tables and, for
+ * IGA_COEF_BSPLINE, a copy of theta.  Errors: IGA_ERR_ARG for unsupported
+ * dim / p / n_el / map / quad_pts or a non-positive det J found at a
+ * quadrature point. Synchronous. */
+int iga_space_create(const iga_space_desc* desc, iga_space** out);
+int iga_space_destroy(iga_space* space);
+int iga_space_info_get(const iga_space* space, iga_space_info* out);
+
+/* ---- surrogate assembly -----------------------------------------------
+ * surrogate_assemble(p, q, M): sample rows by the rule of Sec. 5.1 (every
+ * (L-1)/ceil((L-1)/M)-th of the L = m-4p interior points per direction,
+ * rounded half away from zero), true rows at the samples by Gauss
+ * quadrature, degree-q interpolation with de Boor-averaged knots taken from
+ * the samples (Sec. 3.3), true entries of every pair (i,j) with i or j
+ * outside Omega~ by element quadrature of the boundary band, and the fields
+ * of Eq. DefinitionOfSurrogateMatrixSymmetric / ..SymmetricKernel.
+ * p must equal the space's degree; q >= 1; at least q+1 samples per
+ * direction; M >= 1 (M = 1 gives the true matrices up to rounding).
+ * Builds FP64 fields and FP32 copies, and the inverse Jacobi diagonal of M~.
+ * Asynchronous on `stream` except for a final status check (synchronises).
+ */
+int iga_surrogate_assemble(iga_space* space, int p, int q, int M, unsigned flags,
+                           void* stream, iga_ops** out);
+int iga_ops_destroy(iga_ops* ops);
+
+typedef struct iga_ops_info {
+    long long N;
+    long long pitch;        /* row pitch of the fields (elements) */
+    int m, dim, p, q, M;
+    int nK, nM, D;
+    int ns;                 /* samples per direction */
+    int n_band_elements;    /* elements quadrated for the true entries */
+    int n_sample_rows;      /* ns^dim */
+    double t_sample_ms, t_band_ms, t_interp_ms, t_eval_ms, t_total_ms; /* device time */
+} iga_ops_info;
+int iga_ops_info_get(const iga_ops* ops, iga_ops_info* out);
+
+/* Copies the fields of `which` (IGA_OP_K / IGA_OP_M) in `dtype` into dst
+ * (device pointer, nK or nM rows of N elements, packed [f][N]). Async. */
+int iga_ops_copy_fields(const iga_ops* ops, int which, int dtype, void* dst, void* stream);
+/* Copies the sample table of `which` into dst (device pointer, double,
+ * [D][ns^dim], sample index colex): the true row entries at the sample rows.
+ * Needs IGA_KEEP_SAMPLES. Async. */
+int iga_ops_copy_samples(const iga_ops* ops, int which, double* dst, void* stream);
+/* Copies the 0-based sampled indices of one direction to a host array of
+ * ns ints. Synchronous (host data only). */
+int iga_ops_sample_indices(const iga_ops* ops, int* host_dst);
+
+/* ---- matrix-free operators -----------------------------------------------
+ * stencil_apply: y = A x for A = K~ (difference form) or M~, nrhs vectors,
+ * x, y device pointers [nrhs][N] of `dtype` (float or double), y must not
+ * alias x.  Each field element is read once per call for all nrhs vectors.
+ */
+int iga_stencil_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y,
+                      int nrhs, void* stream);
+
+/* mass_solve: Jacobi-PCG on M~ a = b for nrhs right-hand sides (device
+ * pointers [nrhs][N] of `dtype`; x holds the initial guess on entry and the
+ * solution on exit).  Stops each RHS when ||r||_2 <= rtol ||b||_2 (rtol = 0:
+ * exactly max_it iterations).  FP32 dtype: FP32 fields / vectors, FP64
+ * residual and dot products.  Default schedule: one persistent cooperative
+ * launch for all iterations with device-side convergence; IGA_SOLVE_PLAIN:
+ * one launch per phase and a host convergence test per iteration.
+ * iters_out / relres_out: host arrays of nrhs (nullable); writing them
+ * synchronises the stream.  Returns IGA_ERR_NOT_CONVERGED if some RHS
+ * missed rtol (x still holds the last iterate). */
+int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs,
+                   double rtol, int max_it, unsigned flags, int* iters_out,
+                   double* relres_out, void* stream);
+
+/* ---- wave time stepping ------------------------------------------------
+ * Leapfrog for M~ u'' + K~ u = f (unit density, natural boundary
+ * conditions): a^n solves M~ a^n = f^n - K~ u^n by Jacobi-PCG started from
+ * a^{n-1}; u^{n+1} = 2u^n - u^{n-1} + dt^2 a^n, first step u^1 = u^0 + dt^2/2 a^0
+ * (v^0 = 0).  Point source f_i^n = amp r(t_n) B_i(s_src), Ricker
+ * r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), t_n = n dt.
+ * Receivers record d^n = sum_i u_i^n B_i(s_rec) after every step.
+ */
+typedef struct iga_wave_desc {
+    int nshot;                  /* independent shots advanced together (multi-RHS) */
+    int dtype;                  /* IGA_F32 or IGA_F64 */
+    unsigned solve_flags;       /* IGA_SOLVE_PLAIN for the plain schedule */
+    double dt;
+    int init_kind;              /* IGA_INIT_* */
+    const double* pulse_centre; /* host [nshot][dim] parametric centres (GAUSS_PULSE) */
+    double pulse_width;
+    int with_source;            /* 1: Ricker point source per shot */
+    const double* src_pos;      /* host [nshot][dim] parametric source positions */
+    double f0, t0, src_amp;
+    int nrec;                   /* receivers, shared by all shots */
+    const double* rec_pos;      /* host [nrec][dim] parametric receiver positions */
+    int nsteps_max;             /* capacity of the trace buffer (steps) */
+    double cg_rtol;
+    int cg_max_it;
+} iga_wave_desc;
+
+int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);
+int iga_wave_destroy(iga_wave* wave);
+/* Advances every shot by nsteps. Async on stream; returns IGA_ERR_NOT_CONVERGED
+ * (after synchronising) if a CG solve missed its tolerance, IGA_ERR_ARG if the
+ * trace buffer would overflow. */
+int iga_wave_step(iga_wave* wave, int nsteps, void* stream);
+/* Copies u^n (and u^{n-1} if u_prev != NULL) into device buffers [nshot][N] of the
+ * wave's dtype. Async. */
+int iga_wave_get_state(const iga_wave* wave, void* u, void* u_prev, void* stream);
+/* Copies the traces recorded so far to a host array [nshot][nrec][nsteps_done]
+ * (double) and returns the step count in *nsteps_done. Synchronous. */
+int iga_wave_traces(const iga_wave* wave, double* host_dst, int* nsteps_done);
+/* Total CG iterations summed over steps and shots since creation. */
+int iga_wave_cg_iterations(const iga_wave* wave, long long* total);
+
+/* ---- misc ------------------------------------------------------------- */
+const char* iga_last_error(void);
+/* Number of library kernel launches issued since load (for launch accounting). */
+long long iga_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA_H */

@@ -1,0 +1,696 @@
+// Surrogate assembly on the GPU (FP64 arithmetic throughout).
+//
+//  a2  sample_rows_kernel  : true rows M_delta(x~_s), K_delta(x~_s) at every sample
+//                            row (Eq. StencilRoughDefinition), by Gauss quadrature
+//                            over the (p+1)^d elements of supp(phi_s).
+//  a3  band_kernel         : true entries of every pair (i, j) with i or j outside
+//                            Omega~, by element quadrature of the boundary band,
+//                            written straight into the field slots.  Elements are
+//                            launched in (p+1)^d colours (e_k mod (p+1)), so no two
+//                            concurrent elements share a basis function and the
+//                            read-modify-write of a slot needs no atomics
+//                            (deterministic).
+//  a4  interp_dir_kernel   : B-spline interpolation coefficients of every stencil
+//                            function (Sec. 3.3), one direction at a time with the
+//                            precomputed inverse of the 1-D collocation matrix.
+//  a5  eval_kernel         : surrogate values K~_delta(x~_i), M~_delta(x~_i) at every
+//                            interior row whose neighbour i+delta is interior
+//                            (Eq. DefinitionOfSurrogateMatrixSymmetric / ..Kernel).
+//      finalize_kernel     : FP32 copies of the fields, inverse Jacobi diagonal of
+//                            M~, non-finite check.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "geom.cuh"
+#include "host_bspline.h"
+#include "iga_internal.cuh"
+
+namespace iga {
+
+template <int DIM, int P>
+struct Stencil {
+    static constexpr int P1 = P + 1;
+    static constexpr int NLOC = DIM == 2 ? P1 * P1 : P1 * P1 * P1;
+    static constexpr int PP = 2 * P + 1;
+    static constexpr int DD = DIM == 2 ? PP * PP : PP * PP * PP;
+    static constexpr int T0 = (DD - 1) / 2;
+    static constexpr int NS = DIM == 2 ? 3 : 6;   // packed symmetric entries of G
+};
+
+// colex decode of a local index into DIM digits of base `base`
+template <int DIM>
+__device__ __forceinline__ void decode(int idx, int base, int* out) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        out[k] = idx % base;
+        idx /= base;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ bool in_range(const int* i, int lo, int hi) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) ok = ok && (i[k] >= lo) && (i[k] <= hi);
+    return ok;
+}
+
+// grad phi_a(q) and phi_a(q) from the 1-D tables of element e at point g
+template <int DIM, int P>
+__device__ __forceinline__ void local_basis(const GeomParams& gp, const int* e, const int* g,
+                                            const int* a, double* grad, double& val) {
+    double v[DIM], dv[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const int idx = (e[k] * gp.nq + g[k]) * (P + 1) + a[k];
+        v[k] = gp.bval[idx];
+        dv[k] = gp.bder[idx];
+    }
+    val = 1.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) val *= v[k];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        double gk = 1.0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) gk *= (j == k) ? dv[j] : v[j];
+        grad[k] = gk;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void sym_matvec(const double* G, const double* x, double* y) {
+    if (DIM == 2) {
+        y[0] = G[0] * x[0] + G[1] * x[1];
+        y[1] = G[1] * x[0] + G[2] * x[1];
+    } else {
+        y[0] = G[0] * x[0] + G[1] * x[1] + G[2] * x[2];
+        y[1] = G[1] * x[0] + G[3] * x[1] + G[4] * x[2];
+        y[2] = G[2] * x[0] + G[4] * x[1] + G[5] * x[2];
+    }
+}
+
+// ---------------------------------------------------------------- a3: band elements
+template <int DIM, int P>
+__global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double* __restrict__ fK,
+                            double* __restrict__ fM, long long pitch, int lo, int hi, int all_true,
+                            int* status) {
+    using S = Stencil<DIM, P>;
+    extern __shared__ double sm[];
+    const int nq = gp.nq;
+    int nqd = nq;
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) nqd *= nq;
+    double* Gq = sm;                          // [nqd][NS]
+    double* wq = Gq + nqd * S::NS;            // [nqd]
+    double* grad = wq + nqd;                  // [NLOC][nqd][DIM]
+    double* Ggrad = grad + S::NLOC * nqd * DIM;
+    double* val = Ggrad + S::NLOC * nqd * DIM;   // [NLOC][nqd]
+    double* vw = val + S::NLOC * nqd;            // [NLOC][nqd]
+
+    int e[3] = {0, 0, 0};
+    decode<DIM>(elems[blockIdx.x], gp.n_el, e);
+    for (int q = threadIdx.x; q < nqd; q += blockDim.x) {
+        int g[3] = {0, 0, 0};
+        decode<DIM>(q, nq, g);
+        double G[6], wm;
+        const double det = qp_weights(gp, e, g, G, wm);
+        if (!(det > 0.0)) atomicOr(status, 2);
+#pragma unroll
+        for (int k = 0; k < S::NS; ++k) Gq[q * S::NS + k] = G[k];
+        wq[q] = wm;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < S::NLOC * nqd; idx += blockDim.x) {
+        const int a = idx / nqd, q = idx % nqd;
+        int g[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+        decode<DIM>(q, nq, g);
+        decode<DIM>(a, P + 1, al);
+        double gr[DIM], v, Gg[DIM];
+        local_basis<DIM, P>(gp, e, g, al, gr, v);
+        sym_matvec<DIM>(Gq + q * S::NS, gr, Gg);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            grad[(a * nqd + q) * DIM + k] = gr[k];
+            Ggrad[(a * nqd + q) * DIM + k] = Gg[k];
+        }
+        val[a * nqd + q] = v;
+        vw[a * nqd + q] = v * wq[q];
+    }
+    __syncthreads();
+    const int m = gp.m;
+    for (int pidx = threadIdx.x; pidx < S::NLOC * S::NLOC; pidx += blockDim.x) {
+        const int a = pidx / S::NLOC, b = pidx % S::NLOC;
+        int al[3] = {0, 0, 0}, bl[3] = {0, 0, 0};
+        decode<DIM>(a, P + 1, al);
+        decode<DIM>(b, P + 1, bl);
+        int t = 0, i[3] = {0, 0, 0}, j[3] = {0, 0, 0};
+        for (int k = DIM - 1; k >= 0; --k) t = t * S::PP + (bl[k] - al[k] + P);
+        if (t < S::T0) continue;                       // lower triangle: stored at the other row
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            i[k] = e[k] + al[k];
+            j[k] = e[k] + bl[k];
+        }
+        if (!all_true && in_range<DIM>(i, lo, hi) && in_range<DIM>(j, lo, hi)) continue;  // surrogate slot
+        long long li = 0;
+        for (int k = DIM - 1; k >= 0; --k) li = li * m + i[k];
+        double kv = 0.0, mv = 0.0;
+        for (int q = 0; q < nqd; ++q) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) kv += Ggrad[(a * nqd + q) * DIM + k] * grad[(b * nqd + q) * DIM + k];
+            mv += vw[a * nqd + q] * val[b * nqd + q];
+        }
+        if (t > S::T0) fK[(size_t)(t - S::T0 - 1) * pitch + li] += kv;
+        fM[(size_t)(t - S::T0) * pitch + li] += mv;
+    }
+}
+
+// ---------------------------------------------------------------- a2: sample rows
+template <int DIM, int P>
+__global__ void sample_rows_kernel(GeomParams gp, const int* __restrict__ samp, int ns,
+                                   double* __restrict__ sK, double* __restrict__ sM, int* status) {
+    using S = Stencil<DIM, P>;
+    extern __shared__ double sm[];
+    const int nq = gp.nq;
+    int nqd = nq;
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) nqd *= nq;
+    double* accK = sm;                        // [DD]
+    double* accM = accK + S::DD;              // [DD]
+    double* Gq = accM + S::DD;                // [nqd][NS]
+    double* wq = Gq + nqd * S::NS;            // [nqd]
+    double* Ga = wq + nqd;                    // [nqd][DIM]   G grad phi_a
+    double* va = Ga + nqd * DIM;              // [nqd]        phi_a wm
+
+    int sidx[3] = {0, 0, 0}, row[3] = {0, 0, 0};
+    decode<DIM>(blockIdx.x, ns, sidx);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) row[k] = samp[sidx[k]];
+    for (int t = threadIdx.x; t < S::DD; t += blockDim.x) accK[t] = accM[t] = 0.0;
+
+    for (int a = 0; a < S::NLOC; ++a) {
+        int al[3] = {0, 0, 0}, e[3] = {0, 0, 0};
+        decode<DIM>(a, P + 1, al);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) e[k] = row[k] - al[k];   // element with local function a = row
+        __syncthreads();
+        for (int q = threadIdx.x; q < nqd; q += blockDim.x) {
+            int g[3] = {0, 0, 0};
+            decode<DIM>(q, nq, g);
+            double G[6], wm;
+            const double det = qp_weights(gp, e, g, G, wm);
+            if (!(det > 0.0)) atomicOr(status, 2);
+            double gr[DIM], v, Gg[DIM];
+            local_basis<DIM, P>(gp, e, g, al, gr, v);
+            sym_matvec<DIM>(G, gr, Gg);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) Ga[q * DIM + k] = Gg[k];
+            va[q] = v * wm;
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < S::NLOC; b += blockDim.x) {
+            int bl[3] = {0, 0, 0};
+            decode<DIM>(b, P + 1, bl);
+            double kv = 0.0, mv = 0.0;
+            for (int q = 0; q < nqd; ++q) {
+                int g[3] = {0, 0, 0};
+                decode<DIM>(q, nq, g);
+                double gr[DIM], v;
+                local_basis<DIM, P>(gp, e, g, bl, gr, v);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) kv += Ga[q * DIM + k] * gr[k];
+                mv += va[q] * v;
+            }
+            int t = 0;
+            for (int k = DIM - 1; k >= 0; --k) t = t * S::PP + (bl[k] - al[k] + P);
+            accK[t] += kv;   // distinct t for distinct b within one element
+            accM[t] += mv;
+        }
+    }
+    __syncthreads();
+    int nsd = ns;
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) nsd *= ns;
+    for (int t = threadIdx.x; t < S::DD; t += blockDim.x) {
+        sK[(size_t)t * nsd + blockIdx.x] = accK[t];
+        sM[(size_t)t * nsd + blockIdx.x] = accM[t];
+    }
+}
+
+// ---------------------------------------------------------------- a4: interpolation
+// out[t][c] = sum_j Ainv[c_dir][j] in[t][c with c_dir -> j], for all D stencil functions
+__global__ void interp_dir_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                  const double* __restrict__ Ainv, int ns, int dim, int dir, int D) {
+    int nsd = 1;
+    for (int k = 0; k < dim; ++k) nsd *= ns;
+    const long long total = (long long)D * nsd;
+    int stride_dir = 1;
+    for (int k = 0; k < dir; ++k) stride_dir *= ns;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(idx / nsd);
+        const int c = (int)(idx % nsd);
+        const int cd = (c / stride_dir) % ns;
+        const int base = c - cd * stride_dir;
+        const double* src = in + (size_t)t * nsd + base;
+        double acc = 0.0;
+        for (int j = 0; j < ns; ++j) acc += Ainv[cd * ns + j] * src[(size_t)j * stride_dir];
+        out[idx] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- a5: surrogate evaluation
+template <int DIM>
+__global__ void eval_kernel(const double* __restrict__ coef, int ns, const int* __restrict__ espan,
+                            const double* __restrict__ evals, int q, int L, int lo, int m, int p,
+                            int t_first, int field_base, double* __restrict__ fields, long long pitch) {
+    const int t = t_first + blockIdx.y;
+    const int f = t - field_base;
+    const int PP = 2 * p + 1;
+    int delta[3] = {0, 0, 0};
+    {
+        int tt = t;
+        for (int k = 0; k < DIM; ++k) {
+            delta[k] = tt % PP - p;
+            tt /= PP;
+        }
+    }
+    int nsd = ns, Ld = L;
+    for (int k = 1; k < DIM; ++k) {
+        nsd *= ns;
+        Ld *= L;
+    }
+    const double* C = coef + (size_t)t * nsd;
+    const int q1 = q + 1;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < Ld; r += gridDim.x * blockDim.x) {
+        int l[3] = {0, 0, 0};
+        decode<DIM>(r, L, l);
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const int j = l[k] + delta[k];
+            ok = ok && j >= 0 && j < L;
+        }
+        if (!ok) continue;                    // neighbour outside Omega~: true entry from the band
+        double acc = 0.0;
+        if (DIM == 2) {
+            const int s0 = espan[l[0]], s1 = espan[l[1]];
+            const double* e0 = evals + (size_t)l[0] * q1;
+            const double* e1 = evals + (size_t)l[1] * q1;
+            for (int b = 0; b < q1; ++b) {
+                double row = 0.0;
+                for (int a = 0; a < q1; ++a) row += C[(size_t)(s1 + b) * ns + s0 + a] * e0[a];
+                acc += row * e1[b];
+            }
+        } else {
+            const int s0 = espan[l[0]], s1 = espan[l[1]], s2 = espan[l[2]];
+            const double* e0 = evals + (size_t)l[0] * q1;
+            const double* e1 = evals + (size_t)l[1] * q1;
+            const double* e2 = evals + (size_t)l[2] * q1;
+            for (int c = 0; c < q1; ++c) {
+                double plane = 0.0;
+                for (int b = 0; b < q1; ++b) {
+                    double row = 0.0;
+                    for (int a = 0; a < q1; ++a)
+                        row += C[((size_t)(s2 + c) * ns + s1 + b) * ns + s0 + a] * e0[a];
+                    plane += row * e1[b];
+                }
+                acc += plane * e2[c];
+            }
+        }
+        long long li = 0;
+        for (int k = DIM - 1; k >= 0; --k) li = li * m + (lo + l[k]);
+        fields[(size_t)f * pitch + li] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- finalize
+__global__ void finalize_kernel(const double* __restrict__ fK, const double* __restrict__ fM, float* fK32,
+                                float* fM32, double* dinv64, float* dinv32, int nK, int nM, long long N,
+                                long long pitch, int* status) {
+    const long long total_k = (long long)nK * pitch, total_m = (long long)nM * pitch;
+    int bad = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total_k + total_m;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const double v = idx < total_k ? fK[idx] : fM[idx - total_k];
+        if (!isfinite(v)) bad = 1;
+        if (idx < total_k) fK32[idx] = (float)v;
+        else fM32[idx - total_k] = (float)v;
+        if (idx >= total_k && idx - total_k < N) {
+            const double di = 1.0 / v;   // field 0 of M~ is the diagonal
+            dinv64[idx - total_k] = di;
+            dinv32[idx - total_k] = (float)di;
+            if (!(v > 0.0)) bad = 1;
+        }
+    }
+    if (bad) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------- host side
+template <int DIM, int P>
+static int launch_band(const iga_space* s, const int* d_elems, int count, iga_ops* ops, int all_true,
+                       cudaStream_t st) {
+    using S = Stencil<DIM, P>;
+    int nqd = 1;
+    for (int k = 0; k < DIM; ++k) nqd *= s->nq;
+    const size_t smem = sizeof(double) * (nqd * (S::NS + 1) + S::NLOC * nqd * (2 * DIM + 2));
+    if (smem > 200 * 1024) return fail(IGA_ERR_ARG, "band quadrature tables exceed shared memory");
+    static bool attr_set = false;
+    if (!attr_set) {
+        IGA_CUDA(cudaFuncSetAttribute(band_kernel<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        attr_set = true;
+    }
+    band_kernel<DIM, P><<<count, 128, smem, st>>>(s->gp, d_elems, ops->fK64.as<double>(),
+                                                  ops->fM64.as<double>(), ops->pitch, 2 * P, s->m - 2 * P - 1,
+                                                  all_true, ops->status.as<int>());
+    IGA_LAUNCH_CHECK("band_kernel");
+    return IGA_OK;
+}
+
+template <int DIM, int P>
+static int launch_samples(const iga_space* s, const int* d_samp, iga_ops* ops, cudaStream_t st) {
+    using S = Stencil<DIM, P>;
+    int nqd = 1, nsd = 1;
+    for (int k = 0; k < DIM; ++k) {
+        nqd *= s->nq;
+        nsd *= ops->ns;
+    }
+    const size_t smem = sizeof(double) * (2 * S::DD + nqd * (S::NS + 1) + nqd * (DIM + 1));
+    sample_rows_kernel<DIM, P><<<nsd, 64, smem, st>>>(s->gp, d_samp, ops->ns, ops->sK.as<double>(),
+                                                       ops->sM.as<double>(), ops->status.as<int>());
+    IGA_LAUNCH_CHECK("sample_rows_kernel");
+    return IGA_OK;
+}
+
+typedef int (*band_fn)(const iga_space*, const int*, int, iga_ops*, int, cudaStream_t);
+typedef int (*samp_fn)(const iga_space*, const int*, iga_ops*, cudaStream_t);
+
+static band_fn pick_band(int dim, int p) {
+    if (dim == 2) return p == 1 ? launch_band<2, 1> : p == 2 ? launch_band<2, 2> : launch_band<2, 3>;
+    return p == 1 ? launch_band<3, 1> : p == 2 ? launch_band<3, 2> : launch_band<3, 3>;
+}
+static samp_fn pick_samples(int dim, int p) {
+    if (dim == 2) return p == 1 ? launch_samples<2, 1> : p == 2 ? launch_samples<2, 2> : launch_samples<2, 3>;
+    return p == 1 ? launch_samples<3, 1> : p == 2 ? launch_samples<3, 2> : launch_samples<3, 3>;
+}
+
+// Sampled 0-based indices of one direction (Sec. 5.1): L = m-4p interior points,
+// n = ceil((L-1)/M) intervals, offsets round(j (L-1)/n) half away from zero,
+// computed exactly as floor((2 j (L-1) + n) / (2 n)).
+static std::vector<int> sample_rule(int m, int p, int M) {
+    const int lo = 2 * p, L = m - 4 * p;
+    std::vector<int> out;
+    if (L == 1) {
+        out.push_back(lo);
+        return out;
+    }
+    const long long n = (L - 1 + M - 1) / M;
+    for (long long j = 0; j <= n; ++j) out.push_back(lo + (int)((2 * j * (L - 1) + n) / (2 * n)));
+    return out;
+}
+
+struct EventTimer {
+    cudaEvent_t ev[6];
+    bool ok = false;
+    EventTimer() {
+        ok = true;
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    }
+    ~EventTimer() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace iga
+
+using namespace iga;
+
+extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigned flags, void* stream,
+                                      iga_ops** out) {
+    if (!s || !out) return fail(IGA_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (p != s->p) return fail(IGA_ERR_ARG, "p must equal the space degree");
+    const bool true_only = (flags & IGA_TRUE_ONLY) != 0;
+    if (!true_only) {
+        if (q < 1 || q > 7) return fail(IGA_ERR_ARG, "q must be in 1..7");
+        if (M < 1) return fail(IGA_ERR_ARG, "M must be >= 1");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dim = s->dim, m = s->m, D = s->D, T0 = (D - 1) / 2;
+    iga_ops* ops = new (std::nothrow) iga_ops();
+    if (!ops) return fail(IGA_ERR_OOM, "host allocation failed");
+    ops->space = s;
+    ops->p = p;
+    ops->q = q;
+    ops->M = M;
+    ops->dim = dim;
+    ops->m = m;
+    ops->D = D;
+    ops->nK = T0;
+    ops->nM = T0 + 1;
+    ops->N = s->N;
+    ops->pitch = (s->N + 63) / 64 * 64;
+    ops->flags = flags;
+    const long long pitch = ops->pitch;
+    auto bail = [&](int rc) {
+        delete ops;
+        return rc;
+    };
+    int rc = ops->fK64.alloc(sizeof(double) * ops->nK * pitch);
+    if (!rc) rc = ops->fM64.alloc(sizeof(double) * ops->nM * pitch);
+    if (!rc) rc = ops->fK32.alloc(sizeof(float) * ops->nK * pitch);
+    if (!rc) rc = ops->fM32.alloc(sizeof(float) * ops->nM * pitch);
+    if (!rc) rc = ops->dinv64.alloc(sizeof(double) * pitch);
+    if (!rc) rc = ops->dinv32.alloc(sizeof(float) * pitch);
+    if (!rc) rc = ops->status.alloc(sizeof(int) * 4);
+    if (rc) return bail(rc);
+    if (cudaMemsetAsync(ops->fK64.ptr, 0, ops->fK64.bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(ops->fM64.ptr, 0, ops->fM64.bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(ops->status.ptr, 0, ops->status.bytes, st) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "cudaMemsetAsync"));
+
+    EventTimer tm;
+    cudaEventRecord(tm.ev[0], st);
+    // ---- a3: band (or all) elements, grouped by colour
+    const int ne = s->n_el, P1 = p + 1;
+    std::vector<std::vector<int>> colour(1 << 0);
+    int ncol = 1;
+    for (int k = 0; k < dim; ++k) ncol *= P1;
+    colour.assign(ncol, std::vector<int>());
+    long long nel_total = 1;
+    for (int k = 0; k < dim; ++k) nel_total *= ne;
+    for (long long el = 0; el < nel_total; ++el) {
+        int e[3] = {0, 0, 0};
+        long long r = el;
+        bool band = false;
+        int c = 0, cw = 1;
+        for (int k = 0; k < dim; ++k) {
+            e[k] = (int)(r % ne);
+            r /= ne;
+            band = band || e[k] <= 2 * p - 1 || e[k] >= ne - 2 * p;
+            c += (e[k] % P1) * cw;
+            cw *= P1;
+        }
+        if (true_only || band) colour[c].push_back((int)el);
+    }
+    std::vector<int> flat;
+    std::vector<int> offs(ncol + 1, 0);
+    for (int c = 0; c < ncol; ++c) {
+        offs[c] = (int)flat.size();
+        flat.insert(flat.end(), colour[c].begin(), colour[c].end());
+    }
+    offs[ncol] = (int)flat.size();
+    ops->n_band = (int)flat.size();
+    DevBuf d_elems;
+    if ((rc = d_elems.alloc(sizeof(int) * std::max<size_t>(1, flat.size())))) return bail(rc);
+    if (!flat.empty()) {
+        cudaError_t e = cudaMemcpyAsync(d_elems.ptr, flat.data(), sizeof(int) * flat.size(),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpyAsync(elements)"));
+    }
+    band_fn bf = pick_band(dim, p);
+    for (int c = 0; c < ncol; ++c) {
+        const int cnt = offs[c + 1] - offs[c];
+        if (cnt == 0) continue;
+        if ((rc = bf(s, d_elems.as<int>() + offs[c], cnt, ops, true_only ? 1 : 0, st))) return bail(rc);
+    }
+    cudaEventRecord(tm.ev[1], st);
+
+    DevBuf d_samp, d_Ainv, d_espan, d_evals, d_tmp;
+    if (!true_only) {
+        // ---- a0: sampling rule
+        ops->samp = sample_rule(m, p, M);
+        ops->ns = (int)ops->samp.size();
+        const int ns = ops->ns, L = m - 4 * p;
+        if (ns < q + 1) return bail(fail(IGA_ERR_ARG, "need at least q+1 samples per direction"));
+        int nsd = 1;
+        for (int k = 0; k < dim; ++k) nsd *= ns;
+        ops->n_samples = nsd;
+        if ((rc = d_samp.alloc(sizeof(int) * ns))) return bail(rc);
+        cudaMemcpyAsync(d_samp.ptr, ops->samp.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+        if ((rc = ops->sK.alloc(sizeof(double) * D * nsd))) return bail(rc);
+        if ((rc = ops->sM.alloc(sizeof(double) * D * nsd))) return bail(rc);
+        if ((rc = ops->cK.alloc(sizeof(double) * D * nsd))) return bail(rc);
+        if ((rc = ops->cM.alloc(sizeof(double) * D * nsd))) return bail(rc);
+        if ((rc = d_tmp.alloc(sizeof(double) * D * nsd))) return bail(rc);
+        // ---- a2: true rows at the samples
+        if ((rc = pick_samples(dim, p)(s, d_samp.as<int>(), ops, st))) return bail(rc);
+        cudaEventRecord(tm.ev[2], st);
+        // ---- a4: interpolation operators on the host (x~ abscissae, de Boor knots)
+        const double h = 1.0 / s->n_el;
+        std::vector<double> xs(ns);
+        for (int j = 0; j < ns; ++j) xs[j] = (ops->samp[j] + 1 - 0.5 * (p + 1)) * h;
+        std::vector<double> kn = hb::averaged_knots(xs, q), Ainv;
+        if (!hb::collocation_inverse(kn, q, xs, Ainv))
+            return bail(fail(IGA_ERR_ARG, "singular interpolation matrix"));
+        std::vector<int> espan(L);
+        std::vector<double> evals((size_t)L * (q + 1));
+        for (int l = 0; l < L; ++l) {
+            const double x = (2 * p + l + 1 - 0.5 * (p + 1)) * h;
+            const int mu = hb::find_span(kn, q, x);
+            hb::basis_and_derivative(kn, q, mu, x, &evals[(size_t)l * (q + 1)], nullptr);
+            espan[l] = mu - q;
+        }
+        if ((rc = d_Ainv.alloc(sizeof(double) * Ainv.size()))) return bail(rc);
+        if ((rc = d_espan.alloc(sizeof(int) * L))) return bail(rc);
+        if ((rc = d_evals.alloc(sizeof(double) * evals.size()))) return bail(rc);
+        cudaMemcpyAsync(d_Ainv.ptr, Ainv.data(), sizeof(double) * Ainv.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_espan.ptr, espan.data(), sizeof(int) * L, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_evals.ptr, evals.data(), sizeof(double) * evals.size(), cudaMemcpyHostToDevice, st);
+        for (int which = 0; which < 2; ++which) {
+            double* src = which ? ops->sM.as<double>() : ops->sK.as<double>();
+            double* dst = which ? ops->cM.as<double>() : ops->cK.as<double>();
+            // ping-pong so the last direction lands in dst
+            double* bufs[2] = {dst, d_tmp.as<double>()};
+            const double* in = src;
+            for (int dir = 0; dir < dim; ++dir) {
+                double* o = bufs[(dim - 1 - dir) % 2];
+                const long long total = (long long)D * nsd;
+                const int grid = (int)std::min<long long>((total + 255) / 256, 4096);
+                interp_dir_kernel<<<grid, 256, 0, st>>>(in, o, d_Ainv.as<double>(), ns, dim, dir, D);
+                IGA_LAUNCH_CHECK("interp_dir_kernel");
+                in = o;
+            }
+        }
+        cudaEventRecord(tm.ev[3], st);
+        // ---- a5: surrogate values in Omega~
+        long long Ld = 1;
+        for (int k = 0; k < dim; ++k) Ld *= L;
+        const int gx = (int)std::min<long long>((Ld + 255) / 256, 2048);
+        for (int which = 0; which < 2; ++which) {
+            const int t_first = which ? T0 : T0 + 1;
+            const int cnt = D - t_first;
+            const int fbase = which ? T0 : T0 + 1;
+            dim3 grid(gx, cnt);
+            double* coef = which ? ops->cM.as<double>() : ops->cK.as<double>();
+            double* fld = which ? ops->fM64.as<double>() : ops->fK64.as<double>();
+            if (dim == 2)
+                eval_kernel<2><<<grid, 256, 0, st>>>(coef, ns, d_espan.as<int>(), d_evals.as<double>(), q, L,
+                                                     2 * p, m, p, t_first, fbase, fld, pitch);
+            else
+                eval_kernel<3><<<grid, 256, 0, st>>>(coef, ns, d_espan.as<int>(), d_evals.as<double>(), q, L,
+                                                     2 * p, m, p, t_first, fbase, fld, pitch);
+            IGA_LAUNCH_CHECK("eval_kernel");
+        }
+    } else {
+        cudaEventRecord(tm.ev[2], st);
+        cudaEventRecord(tm.ev[3], st);
+    }
+    cudaEventRecord(tm.ev[4], st);
+    {
+        const long long total = (long long)(ops->nK + ops->nM) * pitch;
+        const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+        finalize_kernel<<<grid, 256, 0, st>>>(ops->fK64.as<double>(), ops->fM64.as<double>(),
+                                              ops->fK32.as<float>(), ops->fM32.as<float>(),
+                                              ops->dinv64.as<double>(), ops->dinv32.as<float>(), ops->nK,
+                                              ops->nM, ops->N, pitch, ops->status.as<int>());
+        IGA_LAUNCH_CHECK("finalize_kernel");
+    }
+    cudaEventRecord(tm.ev[5], st);
+    int status[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(status, ops->status.ptr, sizeof(status), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "surrogate_assemble"));
+    if (status[0] & 2) return bail(fail(IGA_ERR_ARG, "non-positive det J at a quadrature point"));
+    if (status[0] & 1) return bail(fail(IGA_ERR_NONFINITE, "non-finite or non-positive mass diagonal"));
+    float t;
+    cudaEventElapsedTime(&t, tm.ev[0], tm.ev[1]);
+    ops->t_band = t;
+    cudaEventElapsedTime(&t, tm.ev[1], tm.ev[2]);
+    ops->t_sample = t;
+    cudaEventElapsedTime(&t, tm.ev[2], tm.ev[3]);
+    ops->t_interp = t;
+    cudaEventElapsedTime(&t, tm.ev[3], tm.ev[4]);
+    ops->t_eval = t;
+    cudaEventElapsedTime(&t, tm.ev[0], tm.ev[5]);
+    ops->t_total = t;
+    if (!(flags & IGA_KEEP_SAMPLES)) {
+        ops->sK.release();
+        ops->sM.release();
+        ops->cK.release();
+        ops->cM.release();
+    }
+    *out = ops;
+    return IGA_OK;
+}
+
+extern "C" int iga_ops_destroy(iga_ops* ops) {
+    delete ops;
+    return IGA_OK;
+}
+
+extern "C" int iga_ops_info_get(const iga_ops* ops, iga_ops_info* out) {
+    if (!ops || !out) return fail(IGA_ERR_ARG, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->N = ops->N;
+    out->pitch = ops->pitch;
+    out->m = ops->m;
+    out->dim = ops->dim;
+    out->p = ops->p;
+    out->q = ops->q;
+    out->M = ops->M;
+    out->nK = ops->nK;
+    out->nM = ops->nM;
+    out->D = ops->D;
+    out->ns = ops->ns;
+    out->n_band_elements = ops->n_band;
+    out->n_sample_rows = ops->n_samples;
+    out->t_sample_ms = ops->t_sample;
+    out->t_band_ms = ops->t_band;
+    out->t_interp_ms = ops->t_interp;
+    out->t_eval_ms = ops->t_eval;
+    out->t_total_ms = ops->t_total;
+    return IGA_OK;
+}
+
+extern "C" int iga_ops_copy_fields(const iga_ops* ops, int which, int dtype, void* dst, void* stream) {
+    if (!ops || !dst) return fail(IGA_ERR_ARG, "null argument");
+    if (which != IGA_OP_K && which != IGA_OP_M) return fail(IGA_ERR_ARG, "which must be K or M");
+    if (dtype != IGA_F32 && dtype != IGA_F64) return fail(IGA_ERR_ARG, "bad dtype");
+    const int nf = which == IGA_OP_K ? ops->nK : ops->nM;
+    const size_t es = dtype == IGA_F64 ? 8 : 4;
+    const DevBuf& src = which == IGA_OP_K ? (dtype == IGA_F64 ? ops->fK64 : ops->fK32)
+                                          : (dtype == IGA_F64 ? ops->fM64 : ops->fM32);
+    IGA_CUDA(cudaMemcpy2DAsync(dst, es * ops->N, src.ptr, es * ops->pitch, es * ops->N, nf,
+                               cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return IGA_OK;
+}
+
+extern "C" int iga_ops_copy_samples(const iga_ops* ops, int which, double* dst, void* stream) {
+    if (!ops || !dst) return fail(IGA_ERR_ARG, "null argument");
+    const DevBuf& src = which == IGA_OP_K ? ops->sK : ops->sM;
+    if (!src.ptr) return fail(IGA_ERR_ARG, "samples not kept (assemble with IGA_KEEP_SAMPLES)");
+    IGA_CUDA(cudaMemcpyAsync(dst, src.ptr, sizeof(double) * ops->D * ops->n_samples, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return IGA_OK;
+}
+
+extern "C" int iga_ops_sample_indices(const iga_ops* ops, int* host_dst) {
+    if (!ops || !host_dst) return fail(IGA_ERR_ARG, "null argument");
+    for (int j = 0; j < ops->ns; ++j) host_dst[j] = ops->samp[j];
+    return IGA_OK;
+}

@@ -1,0 +1,109 @@
+// Internal declarations of the GB300 surrogate-matrix IGA library.
+// Everything here is private to libiga; the public ABI is include/iga.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iga.h"
+
+namespace iga {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+void count_launch(long long n = 1);
+
+#define IGA_CUDA(call)                                             \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::iga::cuda_fail(e_, #call); \
+    } while (0)
+
+#define IGA_LAUNCH_CHECK(what)                                     \
+    do {                                                           \
+        ::iga::count_launch();                                     \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return ::iga::cuda_fail(e_, what);  \
+    } while (0)
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxP = 3;
+constexpr int kMaxQuad = 8;
+
+// Device-side geometry / coefficient / basis-table bundle (passed by value).
+struct GeomParams {
+    int dim, p, n_el, m, nq;
+    int map_kind;
+    double map_param;
+    int coef_kind;
+    double coef_param;
+    const double* theta;   // [n_theta^dim] colex
+    int n_theta, theta_deg;
+    const double* qs;      // [n_el][nq] parametric coordinate of Gauss point g in element e
+    const double* qw;      // [nq] Gauss weight times h
+    const double* bval;    // [n_el][nq][p+1] values of local functions e+a at point g
+    const double* bder;    // [n_el][nq][p+1] derivatives
+    const int* tspan;      // [n_el][nq] first theta function non-zero at the point
+    const double* tval;    // [n_el][nq][theta_deg+1] theta basis values at the point
+};
+
+// Library-owned device buffers are plain cudaMalloc allocations.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    ~DevBuf();
+    int alloc(size_t nbytes);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+}  // namespace iga
+
+struct iga_space {
+    iga_space_desc desc;
+    int dim, p, n_el, m, nq;
+    long long N;
+    int D;
+    std::vector<double> knots;              // host copy of the open uniform knot vector
+    std::vector<double> gauss_x, gauss_w;   // Gauss rule on [0,1]
+    iga::DevBuf theta, qs, qw, bval, bder, tspan, tval;
+    iga::GeomParams gp;
+};
+
+struct iga_ops {
+    const iga_space* space;
+    int p, q, M, dim, m, D, nK, nM, ns;
+    long long N, pitch;
+    unsigned flags;
+    std::vector<int> samp;                   // sampled 0-based indices (one direction)
+    iga::DevBuf fK64, fM64, fK32, fM32;      // fields [nK|nM][pitch]
+    iga::DevBuf dinv64, dinv32;              // inverse Jacobi diagonal of M~
+    iga::DevBuf sK, sM, cK, cM;              // samples / coefficients [D][ns^dim]
+    iga::DevBuf status;                      // int flags: [0] nonfinite
+    iga::DevBuf work;                        // CG workspace of mass_solve (grown on demand)
+    int n_band, n_samples;
+    float t_sample, t_band, t_interp, t_eval, t_total;
+};
+
+namespace iga {
+// kernels implemented in apply.cu / solve.cu, shared launch helpers
+int launch_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y, int nrhs,
+                 cudaStream_t st);
+int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs, double rtol,
+                    int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st,
+                    void* work, size_t work_bytes, long long* iter_acc, int* status_acc);
+size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs);
+// colex decode of stencil offset t into delta (0..dim-1), values in [-p, p]
+inline void decode_offset(int t, int dim, int p, int delta[3]) {
+    int P = 2 * p + 1;
+    for (int k = 0; k < 3; ++k) {
+        delta[k] = (k < dim) ? (t % P) - p : 0;
+        t /= P;
+    }
+}
+}  // namespace iga

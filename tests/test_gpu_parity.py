@@ -1,0 +1,283 @@
+"""CUDA path (through the C ABI) vs the FP64 oracle on the same seeded inputs.
+
+Tolerances:
+* index / layout work (sample indices, zero pattern of the fields) is bit-exact;
+* FP64 floating point: 1e-12 relative to the largest entry of the operator (fields)
+  or to the |A| |x| bound of the row (operator applies);
+* FP32 paths: 2e-5 relative on the same scales.
+The CG-based tests use rtol 1e-13 on both sides so that the solver error stays
+below the comparison tolerance.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle.assembly import stencil_to_csr, true_rows
+from oracle.surrogate import sample_indices
+from oracle.wave import Leapfrog, gaussian_pulse, pcg, point_values
+from tests.oracle_cases import oracle_space, oracle_surrogate
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300 import workloads as W
+
+CASES = {
+    "annulus64_p2": lambda: W.scaled("annulus64_p2"),
+    "annulus40_p3_sincos": lambda: W.scaled("annulus512_p3", n_el=40),
+    "cube20_p2_theta": lambda: W.scaled("cube96_p2", n_el=20),
+    "minimal_p2_q1": lambda: W.scaled("annulus64_p2", n_el=10, q=1, M=100),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_full(name):
+    w = CASES[name]()
+    sp, S = oracle_surrogate(w)
+    rows = sp.all_rows()
+    SK, SM = S.rows(rows)
+    TK, TM = true_rows(sp, rows)
+    return sp, S, SK, SM, TK, TM
+
+
+@functools.lru_cache(maxsize=None)
+def gpu_ops(name, flags=0, M=None):
+    w = CASES[name]()
+    space = W.make_space(w)
+    ops = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"] if M is None else M, flags)
+    return space, ops
+
+
+def fields(ops, which, dtype):
+    info = iga.iga_ops_info_get(ops)
+    nf = info.nK if which == iga.IGA_OP_K else info.nM
+    t = torch.empty((nf, info.N), dtype=torch.float64 if dtype == iga.IGA_F64 else torch.float32,
+                    device="cuda")
+    iga.iga_ops_copy_fields(ops, which, dtype, t)
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def oracle_fields(sp, SK, SM):
+    t0 = (sp.D - 1) // 2
+    return SK[:, t0 + 1:].T, SM[:, t0:].T
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sample_indices_bit_exact(name):
+    w = CASES[name]()
+    _, ops = gpu_ops(name)
+    m = w["n_el"] + w["p"]
+    assert list(iga.iga_ops_sample_indices(ops)) == list(sample_indices(m, w["p"], w["M"]))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fields_fp64_match_oracle(name):
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    oK, oM = oracle_fields(sp, SK, SM)
+    gK, gM = fields(ops, iga.IGA_OP_K, iga.IGA_F64), fields(ops, iga.IGA_OP_M, iga.IGA_F64)
+    # layout: the zero pattern (columns outside the grid) is identical
+    assert np.array_equal(gK == 0.0, oK == 0.0)
+    assert np.array_equal(gM == 0.0, oM == 0.0)
+    assert np.abs(gK - oK).max() <= 1e-12 * np.abs(oK).max()
+    assert np.abs(gM - oM).max() <= 1e-12 * np.abs(oM).max()
+
+
+@pytest.mark.parametrize("name", ["annulus64_p2", "cube20_p2_theta"])
+def test_fields_fp32_are_rounded_fp64(name):
+    _, ops = gpu_ops(name)
+    for which in (iga.IGA_OP_K, iga.IGA_OP_M):
+        f64 = fields(ops, which, iga.IGA_F64)
+        f32 = fields(ops, which, iga.IGA_F32)
+        assert np.array_equal(f32, f64.astype(np.float32))
+
+
+@pytest.mark.parametrize("name", ["annulus40_p3_sincos", "cube20_p2_theta"])
+def test_sample_tables_match_oracle(name):
+    sp, S, *_ = oracle_full(name)
+    _, ops = gpu_ops(name, flags=iga.IGA_KEEP_SAMPLES)
+    info = iga.iga_ops_info_get(ops)
+    for which, ref in ((iga.IGA_OP_K, S.sK), (iga.IGA_OP_M, S.sM)):
+        t = torch.empty((info.D, info.n_sample_rows), dtype=torch.float64, device="cuda")
+        iga.iga_ops_copy_samples(ops, which, t)
+        got = t.cpu().numpy()
+        want = np.stack([inputs.colex(ref[k]) for k in range(info.D)])
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", ["annulus64_p2", "cube20_p2_theta"])
+def test_true_only_matches_oracle_true_matrix(name):
+    sp, _, _, _, TK, TM = oracle_full(name)
+    _, ops = gpu_ops(name, flags=iga.IGA_TRUE_ONLY)
+    oK, oM = oracle_fields(sp, TK, TM)
+    gK, gM = fields(ops, iga.IGA_OP_K, iga.IGA_F64), fields(ops, iga.IGA_OP_M, iga.IGA_F64)
+    assert np.abs(gK - oK).max() <= 1e-12 * np.abs(oK).max()
+    assert np.abs(gM - oM).max() <= 1e-12 * np.abs(oM).max()
+
+
+def test_sampling_length_one_reproduces_true_matrix_on_gpu():
+    _, ops1 = gpu_ops("annulus40_p3_sincos", M=1)
+    _, opsT = gpu_ops("annulus40_p3_sincos", flags=iga.IGA_TRUE_ONLY)
+    for which in (iga.IGA_OP_K, iga.IGA_OP_M):
+        a, b = fields(ops1, which, iga.IGA_F64), fields(opsT, which, iga.IGA_F64)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_assembly_is_deterministic():
+    w = CASES["cube20_p2_theta"]()
+    space = W.make_space(w)
+    a = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"])
+    b = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"])
+    for which in (iga.IGA_OP_K, iga.IGA_OP_M):
+        assert np.array_equal(fields(a, which, iga.IGA_F64), fields(b, which, iga.IGA_F64))
+    iga.iga_ops_destroy(a)
+    iga.iga_ops_destroy(b)
+
+
+def _apply_case(name, which, dtype, nrhs):
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    A = stencil_to_csr(sp, SK if which == iga.IGA_OP_K else SM)
+    x = inputs.vectors(sp.N, nrhs)
+    tdt = torch.float64 if dtype == iga.IGA_F64 else torch.float32
+    xg = torch.tensor(x, dtype=tdt, device="cuda")
+    yg = torch.empty_like(xg)
+    iga.iga_stencil_apply(ops, which, dtype, xg, yg, nrhs)
+    torch.cuda.synchronize()
+    y = yg.cpu().numpy().astype(np.float64)
+    xr = x if dtype == iga.IGA_F64 else x.astype(np.float32).astype(np.float64)
+    ref = (A @ xr.T).T
+    bound = (abs(A) @ np.abs(xr).T).T
+    return y, ref, bound
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("which", ["K", "M"])
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_stencil_apply_fp64(name, which, nrhs):
+    w = iga.IGA_OP_K if which == "K" else iga.IGA_OP_M
+    y, ref, bound = _apply_case(name, w, iga.IGA_F64, nrhs)
+    assert np.all(np.abs(y - ref) <= 1e-12 * bound + 1e-300)
+
+
+@pytest.mark.parametrize("name", ["annulus64_p2", "annulus40_p3_sincos", "cube20_p2_theta"])
+@pytest.mark.parametrize("which", ["K", "M"])
+def test_stencil_apply_fp32(name, which):
+    w = iga.IGA_OP_K if which == "K" else iga.IGA_OP_M
+    y, ref, bound = _apply_case(name, w, iga.IGA_F32, 4)
+    assert np.all(np.abs(y - ref) <= 2e-5 * bound + 1e-30)
+
+
+def test_stencil_apply_zero_rhs_and_alias():
+    _, ops = gpu_ops("annulus64_p2")
+    x = torch.zeros(4356, dtype=torch.float64, device="cuda")
+    iga.iga_stencil_apply(ops, iga.IGA_OP_K, iga.IGA_F64, x, x.clone(), 0)
+    with pytest.raises(iga.IgaError):
+        iga.iga_stencil_apply(ops, iga.IGA_OP_K, iga.IGA_F64, x, x, 1)
+
+
+@pytest.mark.parametrize("name", ["annulus64_p2", "cube20_p2_theta"])
+def test_mass_solve_fp64_matches_direct_solve(name):
+    import scipy.sparse.linalg as spla
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    M = stencil_to_csr(sp, SM).tocsc()
+    b = inputs.vectors(sp.N, 5)
+    ref = np.stack([spla.spsolve(M, bb) for bb in b])
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, bg, xg, 5, 1e-13, 2000)
+    x = xg.cpu().numpy()
+    assert np.all(rel <= 1e-13) and np.all(iters > 0)
+    assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_mass_solve_iterates_match_oracle_pcg():
+    """Fixed iteration count (rtol = 0): GPU and oracle run the identical recurrence."""
+    sp, S, SK, SM, _, _ = oracle_full("annulus40_p3_sincos")
+    _, ops = gpu_ops("annulus40_p3_sincos")
+    M = stencil_to_csr(sp, SM)
+    b = inputs.vectors(sp.N, 1)[0]
+    x0 = 0.1 * inputs.vectors(sp.N, 1, seed=99)[0]
+    xr, it, _ = pcg(M, b, x0.copy(), 1.0 / M.diagonal(), 0.0, 25)
+    bg = torch.tensor(b[None], device="cuda")
+    xg = torch.tensor(x0[None], device="cuda")
+    rc, iters, _ = iga.iga_mass_solve(ops, iga.IGA_F64, bg, xg, 1, 0.0, 25)
+    assert iters[0] == 25 and it == 25
+    assert np.abs(xg.cpu().numpy()[0] - xr).max() <= 1e-11 * np.abs(xr).max()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_mass_solve_plain_and_persistent_schedules_agree_bitwise(dtype):
+    _, ops = gpu_ops("cube20_p2_theta")
+    info = iga.iga_ops_info_get(ops)
+    dt = iga.IGA_F64 if dtype == "f64" else iga.IGA_F32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    b = torch.tensor(inputs.vectors(info.N, 3), dtype=tdt, device="cuda")
+    x1 = torch.zeros_like(b)
+    x2 = torch.zeros_like(b)
+    rtol = 1e-12 if dtype == "f64" else 1e-6
+    _, i1, r1 = iga.iga_mass_solve(ops, dt, b, x1, 3, rtol, 500)
+    _, i2, r2 = iga.iga_mass_solve(ops, dt, b, x2, 3, rtol, 500, flags=iga.IGA_SOLVE_PLAIN)
+    assert list(i1) == list(i2)
+    assert torch.equal(x1, x2)
+
+
+def test_mass_solve_zero_rhs_gives_zero():
+    _, ops = gpu_ops("annulus64_p2")
+    b = torch.zeros((1, 4356), dtype=torch.float64, device="cuda")
+    x = torch.ones_like(b)
+    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, b, x, 1, 1e-10, 100)
+    assert iters[0] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_mass_solve_reports_non_convergence():
+    _, ops = gpu_ops("annulus64_p2")
+    b = torch.tensor(inputs.vectors(4356, 1), device="cuda")
+    x = torch.zeros_like(b)
+    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, b, x, 1, 1e-12, 2, allow_not_converged=True)
+    assert rc == iga.IGA_ERR_NOT_CONVERGED and iters[0] == 2 and rel[0] > 1e-12
+
+
+def _wave_case(dtype, nsteps=20):
+    name = "annulus64_p2"
+    w = CASES[name]()
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    dt = W.dt_of(w)
+    centre = inputs.pulse_centre(2)
+    rec = np.array([[0.3, 0.2], [0.7, 0.9], [0.0, 0.5]])
+    wave = iga.iga_wave_create(ops, 1, dtype, dt, init_kind=iga.IGA_INIT_GAUSS_PULSE,
+                               pulse_centre=centre[None], pulse_width=0.05, rec_pos=rec,
+                               nsteps_max=nsteps, cg_rtol=1e-13 if dtype == iga.IGA_F64 else 1e-6,
+                               cg_max_it=3000)
+    iga.iga_wave_step(wave, nsteps)
+    tdt = torch.float64 if dtype == iga.IGA_F64 else torch.float32
+    u = torch.empty((1, sp.N), dtype=tdt, device="cuda")
+    iga.iga_wave_get_state(wave, u)
+    torch.cuda.synchronize()
+    traces = iga.iga_wave_traces(wave, 1, len(rec), nsteps)
+    iga.iga_wave_destroy(wave)
+    lf = Leapfrog(sp, SK, SM, dt, rtol=1e-13, max_it=3000)
+    xc = sp.geometry(centre)[0]
+    u0 = gaussian_pulse(sp, xc, 0.05)
+    ur, _, tr = lf.run(u0, nsteps, receivers=list(rec))
+    return u.cpu().numpy()[0].astype(np.float64), ur, traces[0], tr
+
+
+def test_wave_fp64_matches_oracle():
+    u, ur, tr, trr = _wave_case(iga.IGA_F64)
+    assert np.linalg.norm(u - ur) <= 1e-11 * np.linalg.norm(ur)
+    assert np.abs(tr - trr).max() <= 1e-11 * np.abs(trr).max()
+
+
+def test_wave_fp32_error_against_fp64_oracle():
+    u, ur, tr, trr = _wave_case(iga.IGA_F32)
+    err = np.linalg.norm(u - ur) / np.linalg.norm(ur)
+    print("FP32 leapfrog relative L2 error after 20 steps:", err)
+    assert err <= 1e-5
