@@ -88,9 +88,13 @@ class Surrogate:
         self.cM = np.array([self._coefficients(v) for v in self.sM])
 
     def _coefficients(self, vals):
+        """Tensor interpolation: solve A C = values along each direction in turn."""
         C = vals
         for k in range(self.space.dim):
-            C = np.moveaxis(np.linalg.solve(self.A, np.moveaxis(C, k, 0)), 0, k)
+            Ck = np.moveaxis(C, k, 0)
+            shp = Ck.shape
+            Ck = np.linalg.solve(self.A, Ck.reshape(shp[0], -1)).reshape(shp)
+            C = np.moveaxis(Ck, 0, k)
         return C
 
     def evaluate(self, which, t, points):

@@ -221,30 +221,54 @@ def test_sampling_rule_config1_and_rounding():
         assert np.all(np.diff(s) <= int(np.ceil((m - 4 * p - 1) / np.ceil((m - 4 * p - 1) / M))))
 
 
-def test_interpolation_matches_scipy_with_same_knots():
-    sp = Space(2, 2, 40, AnnulusQuarter(), SinCosCoef())
-    S = Surrogate(sp, 3, 5)
-    t = 17
-    vals = S.sK[t]
-    spl1 = make_interp_spline(S.xs, vals, k=3, t=S.iknots, axis=0)
-    C1 = spl1.c
-    spl2 = make_interp_spline(S.xs, C1, k=3, t=S.iknots, axis=1)
-    # scipy stores the interpolation axis first: spl2.c is indexed [c_2, c_1]
-    np.testing.assert_allclose(spl2.c.T, S.cK[t], rtol=1e-11, atol=1e-13 * np.abs(vals).max())
-    knots = interp_knots(S.xs, 3)
-    assert len(knots) == len(S.xs) + 4
-
-
-def _surrogate_case():
-    sp = Space(2, 2, 64, AnnulusQuarter(), SinCosCoef(0.5))
+def _interp_case(dim):
+    if dim == 2:
+        sp = Space(2, 2, 40, AnnulusQuarter(), SinCosCoef())
+        return sp, Surrogate(sp, 3, 5)
+    sp = Space(3, 2, 20, CubeSinePerturbed(0.1), BsplineThetaCoef(inputs.theta_lognormal(n=6)))
     return sp, Surrogate(sp, 2, 4)
 
 
-def test_surrogate_equals_true_at_sample_rows():
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interpolation_matches_scipy_with_same_knots(dim):
+    """Coefficients equal scipy's interpolating spline applied direction by direction."""
+    sp, S = _interp_case(dim)
+    t = sp.D // 2 + 3
+    vals = S.sK[t]
+    C = vals
+    for k in range(dim):
+        spl = make_interp_spline(S.xs, np.moveaxis(C, k, 0), k=S.q, t=S.iknots, axis=0)
+        C = np.moveaxis(spl.c, 0, k)          # scipy puts the interpolation axis first
+    np.testing.assert_allclose(C, S.cK[t], rtol=1e-11, atol=1e-13 * np.abs(vals).max())
+    knots = interp_knots(S.xs, S.q)
+    assert len(knots) == len(S.xs) + S.q + 1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interpolant_reproduces_samples_in_every_dimension(dim):
+    """Sec. 3.3: the surrogate stencil function interpolates the sampled values."""
+    sp, S = _interp_case(dim)
+    grids = np.meshgrid(*([S.samp] * dim), indexing='ij')
+    pts = np.stack([g.ravel() for g in grids], axis=1)
+    for t in (sp.D // 2, sp.D - 1, sp.D // 2 + 5):
+        got = S.evaluate('K', t, pts).reshape((len(S.samp),) * dim)
+        np.testing.assert_allclose(got, S.sK[t], rtol=1e-12, atol=1e-14 * np.abs(S.sK[t]).max())
+
+
+def _surrogate_case(dim=2):
+    if dim == 2:
+        sp = Space(2, 2, 64, AnnulusQuarter(), SinCosCoef(0.5))
+        return sp, Surrogate(sp, 2, 4)
+    sp = Space(3, 2, 20, CubeSinePerturbed(0.1), BsplineThetaCoef(inputs.theta_lognormal(n=6)))
+    return sp, Surrogate(sp, 2, 4)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_surrogate_equals_true_at_sample_rows(dim):
     """Interpolation reproduces the sampled values (Sec. 3.3): upper entries and the mass diagonal."""
-    sp, S = _surrogate_case()
-    g = np.meshgrid(S.samp, S.samp, indexing='ij')
-    rows = np.stack([g[0].ravel(), g[1].ravel()], 1)
+    sp, S = _surrogate_case(dim)
+    g = np.meshgrid(*([S.samp] * dim), indexing='ij')
+    rows = np.stack([gg.ravel() for gg in g], 1)
     SK, SM = S.rows(rows)
     TK, TM = true_rows(sp, rows)
     t0 = (sp.D - 1) // 2
