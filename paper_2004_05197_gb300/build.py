@@ -16,6 +16,9 @@ SOURCES = ["space.cu", "assemble.cu", "apply.cu", "solve.cu", "wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
+# IGA_BOUNDS_CHECK=1 builds the self-checking variant (bounds-checked CG accesses)
+if os.environ.get("IGA_BOUNDS_CHECK") == "1":
+    FLAGS = FLAGS + ["-DIGA_BOUNDS_CHECK"]
 
 
 def nvcc():

@@ -22,6 +22,7 @@
 // scalars read back to the host every phase (the plain reference schedule).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -31,6 +32,23 @@
 #include "stencil.cuh"
 
 namespace iga {
+
+// Optional self-checking build (-DIGA_BOUNDS_CHECK): every global access of the
+// CG path is checked against the extent of its buffer; the first violation is
+// recorded (site, index, extent) and the access is skipped instead of faulting.
+__device__ long long g_bounds_record[4];
+#ifdef IGA_BOUNDS_CHECK
+__device__ __noinline__ void bounds_record(long long idx, long long ext, int site) {
+    if (atomicCAS((unsigned long long*)&g_bounds_record[0], 0ull, (unsigned long long)site) == 0ull) {
+        g_bounds_record[1] = idx;
+        g_bounds_record[2] = ext;
+    }
+}
+#define IGA_IN(idx, ext, site) \
+    (((long long)(idx) >= 0 && (long long)(idx) < (long long)(ext)) ? true : (bounds_record((idx), (ext), (site)), false))
+#else
+#define IGA_IN(idx, ext, site) true
+#endif
 
 constexpr int kCgThreads = 256;
 constexpr int kCgWarps = kCgThreads / 32;
@@ -44,16 +62,22 @@ template <typename T>
 struct PlainLoad {
     const T* x;
     long long xs;
-    __device__ __forceinline__ T operator()(int r, int idx) const { return x[r * xs + idx]; }
+    long long ext;
+    __device__ __forceinline__ T operator()(int r, int idx) const {
+        const long long o = r * xs + idx;
+        return IGA_IN(o, ext, 1) ? x[o] : T(0);
+    }
 };
 template <typename T, int R>
 struct CombLoad {   // z + beta p_old, formed on the fly
     const T* z;
     const T* p;
     long long xs;
+    long long ext;
     T beta[R];
     __device__ __forceinline__ T operator()(int r, int idx) const {
-        return fma(beta[r], p[r * xs + idx], z[r * xs + idx]);
+        const long long o = r * xs + idx;
+        return IGA_IN(o, ext, 2) ? fma(beta[r], p[o], z[o]) : T(0);
     }
 };
 
@@ -62,7 +86,9 @@ template <int DIM, int P, typename T, int R, class Load>
 __device__ __forceinline__ void mass_row(const T* __restrict__ F, long long pitch, const Load& ld, int i, int N,
                                          int m, T* acc, T* own) {
     constexpr int NF = StencilShape<DIM, P>::T0;
-    const T d = __ldg(F + i);
+    const long long fext = (long long)(NF + 1) * pitch;
+    (void)fext;
+    const T d = IGA_IN(i, fext, 3) ? __ldg(F + i) : T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         own[r] = ld(r, i);
@@ -75,8 +101,8 @@ __device__ __forceinline__ void mass_row(const T* __restrict__ F, long long pitc
         const T* Fu = Foff + (size_t)u * pitch;
         const int ip = i + dl, im = i - dl;
         const bool okp = ip < N, okm = im >= 0;
-        const T s = __ldg(Fu + i);
-        const T sm = okm ? __ldg(Fu + im) : T(0);
+        const T s = IGA_IN((long long)(u + 1) * pitch + i, fext, 4) ? __ldg(Fu + i) : T(0);
+        const T sm = (okm && IGA_IN((long long)(u + 1) * pitch + im, fext, 5)) ? __ldg(Fu + im) : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const T xp = okp ? ld(r, ip) : T(0);
@@ -115,7 +141,10 @@ __device__ __forceinline__ void grid_sum(const double* partials, int nblocks, in
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = w; k < K; k += kCgWarps) {
         double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32) s += __ldcg(partials + (size_t)b * stride + off + k);
+        for (int b = lane; b < nblocks; b += 32)
+            s += IGA_IN((long long)b * stride + off + k, (long long)nblocks * stride, 14)
+                     ? __ldcg(partials + (size_t)b * stride + off + k)
+                     : 0.0;
 #pragma unroll
         for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, off2);
         if (lane == 0) out[k] = s;
@@ -166,24 +195,30 @@ struct CgVecs {
     T* p1;
     T* q;
     int N, m;
+    long long ext_vec;   // R * N: extent of every [R][N] vector
+    long long ext_diag;  // extent of dinv
 };
 
 // init: r = b - M~x, z = D^-1 r; partials (r,z), (r,r), (b,b)
 template <int DIM, int P, typename T, int R>
 __device__ __forceinline__ void cg_init_rows(const CgVecs<T>& v, double* part) {
     for (int k = 0; k < 3 * R; ++k) part[k] = 0.0;
-    PlainLoad<T> ld{v.x, v.N};
+    PlainLoad<T> ld{v.x, v.N, v.ext_vec};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
         mass_row<DIM, P, T, R>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
-        const double di = (double)v.dinv[i];
+        const double di = IGA_IN(i, v.ext_diag, 6) ? (double)v.dinv[i] : 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const double bi = (double)v.b[(size_t)r * v.N + i];
+            const long long o = (long long)r * v.N + i;
+            const bool ok = IGA_IN(o, v.ext_vec, 7);
+            const double bi = ok ? (double)v.b[o] : 0.0;
             const double ri = bi - (double)acc[r];
             const T zi = (T)(di * ri);
-            v.r[(size_t)r * v.N + i] = ri;
-            v.z[(size_t)r * v.N + i] = zi;
+            if (ok) {
+                v.r[o] = ri;
+                v.z[o] = zi;
+            }
             part[3 * r + 0] += ri * (double)zi;
             part[3 * r + 1] += ri * ri;
             part[3 * r + 2] += bi * bi;
@@ -200,6 +235,7 @@ __device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T*
     ld.z = v.z;
     ld.p = pold;
     ld.xs = v.N;
+    ld.ext = v.ext_vec;
 #pragma unroll
     for (int r = 0; r < R; ++r) ld.beta[r] = (T)beta[r];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
@@ -208,8 +244,11 @@ __device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T*
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!active[r]) continue;
-            pnew[(size_t)r * v.N + i] = own[r];
-            v.q[(size_t)r * v.N + i] = acc[r];
+            const long long o = (long long)r * v.N + i;
+            if (IGA_IN(o, v.ext_vec, 8)) {
+                pnew[o] = own[r];
+                v.q[o] = acc[r];
+            }
             part[r] += (double)own[r] * (double)acc[r];
         }
     }
@@ -221,11 +260,12 @@ __device__ __forceinline__ void cg_phase_b(const CgVecs<T>& v, const T* pnew, co
                                            const int* active, double* part) {
     for (int k = 0; k < 2 * R; ++k) part[k] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
-        const double di = (double)v.dinv[i];
+        const double di = IGA_IN(i, v.ext_diag, 9) ? (double)v.dinv[i] : 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!active[r]) continue;
             const size_t o = (size_t)r * v.N + i;
+            if (!IGA_IN(o, v.ext_vec, 10)) continue;
             const T pi = pnew[o];
             v.x[o] = v.x[o] + (T)alpha[r] * pi;
             const double ri = v.r[o] - alpha[r] * (double)v.q[o];
@@ -267,7 +307,8 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
 
     cg_init_rows<DIM, P, T, R>(v, part);
     block_sum<3 * R>(part, wsum, red);
-    if (threadIdx.x < 3 * R) c.partials[(size_t)blockIdx.x * S + 3 * R + threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x < 3 * R && IGA_IN((long long)blockIdx.x * S + 3 * R + threadIdx.x, (long long)c.nblocks * S, 11))
+        c.partials[(size_t)blockIdx.x * S + 3 * R + threadIdx.x] = red[threadIdx.x];
     if (!grid_barrier(c.bar, c.err)) return;
     grid_sum<3 * R>(c.partials, gridDim.x, S, 3 * R, red);
     if (threadIdx.x < R) {
@@ -285,7 +326,7 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
     for (int r = 0; r < R; ++r)
         if (!(bnorm[r] > 0.0))
             for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x)
-                v.x[(size_t)r * v.N + i] = T(0);
+                if (IGA_IN((long long)r * v.N + i, v.ext_vec, 15)) v.x[(size_t)r * v.N + i] = T(0);
     // p_old starts at 0 (cleared by the host) so that p = z on the first iteration
     for (int it = 0; it < c.max_it; ++it) {
         bool any = false;
@@ -295,7 +336,8 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
         T* pnew = (it & 1) ? v.p0 : v.p1;
         cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part);
         block_sum<R>(part, wsum, red);
-        if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + threadIdx.x] = red[threadIdx.x];
+        if (threadIdx.x < R && IGA_IN((long long)blockIdx.x * S + threadIdx.x, (long long)c.nblocks * S, 12))
+            c.partials[(size_t)blockIdx.x * S + threadIdx.x] = red[threadIdx.x];
         if (!grid_barrier(c.bar, c.err)) return;
         grid_sum<R>(c.partials, gridDim.x, S, 0, red);
         if (threadIdx.x < R) {
@@ -312,7 +354,8 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
         __syncthreads();
         cg_phase_b<T, R>(v, pnew, alpha, active, part);
         block_sum<2 * R>(part, wsum, red);
-        if (threadIdx.x < 2 * R) c.partials[(size_t)blockIdx.x * S + R + threadIdx.x] = red[threadIdx.x];
+        if (threadIdx.x < 2 * R && IGA_IN((long long)blockIdx.x * S + R + threadIdx.x, (long long)c.nblocks * S, 13))
+            c.partials[(size_t)blockIdx.x * S + R + threadIdx.x] = red[threadIdx.x];
         if (!grid_barrier(c.bar, c.err)) return;
         grid_sum<2 * R>(c.partials, gridDim.x, S, R, red);
         if (threadIdx.x < R) {
@@ -477,6 +520,8 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, double rtol, int max_
     v.q = (T*)w.q;
     v.N = (int)N;
     v.m = ops->m;
+    v.ext_vec = (long long)R * N;
+    v.ext_diag = ops->pitch;
     IGA_CUDA(cudaMemsetAsync(w.p0, 0, sizeof(T) * R * N, st));
     IGA_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
     IGA_CUDA(cudaMemsetAsync(w.err, 0, 64, st));
@@ -499,6 +544,18 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, double rtol, int max_
                                                     kCgThreads, args, 0, st);
         count_launch();
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(pcg)");
+#ifdef IGA_BOUNDS_CHECK
+        {
+            long long rec[4] = {0, 0, 0, 0};
+            IGA_CUDA(cudaStreamSynchronize(st));
+            IGA_CUDA(cudaMemcpyFromSymbol(rec, g_bounds_record, sizeof(rec)));
+            if (rec[0] != 0) {
+                char msg[160];
+                snprintf(msg, sizeof(msg), "bounds check: site %lld index %lld extent %lld", rec[0], rec[1], rec[2]);
+                return fail(IGA_ERR_ARG, msg);
+            }
+        }
+#endif
         if (iters_h || relres_h || not_conv) {
             int err = 0;
             IGA_CUDA(cudaMemcpyAsync(iters, w.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
