@@ -99,14 +99,19 @@ __device__ __forceinline__ void mass_row(const T* __restrict__ F, long long pitc
     for (int u = 0; u < NF; ++u) {
         const int dl = field_delta<DIM, P>(u, m);
         const T* Fu = Foff + (size_t)u * pitch;
+        // clamp out-of-range neighbours to the row itself (addresses always valid), then mask
         const int ip = i + dl, im = i - dl;
         const bool okp = ip < N, okm = im >= 0;
+        const int ipc = okp ? ip : i, imc = okm ? im : i;
         const T s = IGA_IN((long long)(u + 1) * pitch + i, fext, 4) ? __ldg(Fu + i) : T(0);
-        const T sm = (okm && IGA_IN((long long)(u + 1) * pitch + im, fext, 5)) ? __ldg(Fu + im) : T(0);
+        const T smv = IGA_IN((long long)(u + 1) * pitch + imc, fext, 5) ? __ldg(Fu + imc) : T(0);
+        const T sm = okm ? smv : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const T xp = okp ? ld(r, ip) : T(0);
-            const T xm = okm ? ld(r, im) : T(0);
+            const T xpv = ld(r, ipc);
+            const T xmv = ld(r, imc);
+            const T xp = okp ? xpv : T(0);
+            const T xm = okm ? xmv : T(0);
             acc[r] = fma(s, xp, acc[r]);
             acc[r] = fma(sm, xm, acc[r]);
         }

@@ -13,7 +13,8 @@
 //   M~: (M~x)_i = F_diag[i] x_i + sum_u F_u[i] x_{i+Delta_u} + F_u[i-Delta_u] x_{i-Delta_u}
 //
 // Entries whose column leaves the index grid are stored as 0, so a wrapped
-// linear neighbour contributes nothing; only the linear range [0, N) is guarded.
+// linear neighbour contributes nothing; only the linear range [0, N) is guarded,
+// by clamping the neighbour index (every address stays inside its buffer).
 #pragma once
 
 #include "iga_internal.cuh"
@@ -59,14 +60,20 @@ __device__ __forceinline__ void stencil_row(const T* __restrict__ F, long long p
     for (int u = 0; u < NF; ++u) {
         const int dl = field_delta<DIM, P>(u, m);
         const T* Fu = Foff + (size_t)u * pitch;
+        // neighbour indices are clamped to the row itself when they leave [0, N),
+        // so every address formed is inside its buffer; the value is then masked
         const int ip = i + dl, im = i - dl;
         const bool okp = ip < N, okm = im >= 0;
+        const int ipc = okp ? ip : i, imc = okm ? im : i;
         const T s = __ldg(Fu + i);
-        const T sm = okm ? __ldg(Fu + im) : T(0);
+        const T smv = __ldg(Fu + imc);
+        const T sm = okm ? smv : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const T xp = okp ? __ldg(x + r * xs + ip) : T(0);
-            const T xm = okm ? __ldg(x + r * xs + im) : T(0);
+            const T xpv = __ldg(x + r * xs + ipc);
+            const T xmv = __ldg(x + r * xs + imc);
+            const T xp = okp ? xpv : T(0);
+            const T xm = okm ? xmv : T(0);
             if (MASS) {
                 acc[r] = fma(s, xp, acc[r]);
                 acc[r] = fma(sm, xm, acc[r]);
