@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the surrogate-matrix IGA wave hot path on GB300.
+
+One bench step is one pass of the whole hot path over the workload: surrogate
+assembly (index sets, sample-row quadrature, band quadrature, interpolation,
+surrogate evaluation) followed by `nsteps` leapfrog steps (K~ apply, Jacobi-PCG
+on M~, update, receivers), all on the device.
+
+Default workload: cube96_p2 (3-D p=2, 96^3 elements, sine-perturbed cube,
+lognormal wave speed on a 16^3 cubic B-spline grid, q=2, M=6, Ricker source at
+the centre, 500 FP32 time steps).  Its stencil fields (1.4 GB FP32 + FP64)
+exceed the L2 cache, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs under torchrun as independent
+replicas (one per GPU, no collective on the data path; weak scaling).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+# the CPU oracle legs run single-threaded (the thread count is reported)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "surrogate rows/s; wave shot-steps/s FP32-batched vs FP64 plain; % HBM peak"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cg_bytes(nM, R, es):
+    """Algorithmic HBM bytes per row of one persistent PCG launch (fields once per pass).
+
+    init : fields nM*es + D^-1 es + per RHS (x, b, z: es each; r: 8)
+    iter : phase A fields nM*es + per RHS (z, p_old read; p_new, q write: 4 es)
+           phase B D^-1 es + per RHS (p_new, q, x read, x, z write: 5 es; r read+write: 16)
+    """
+    init = nM * es + es + R * (3 * es + 8)
+    it = nM * es + es + R * (9 * es + 16)
+    return init, it
+
+
+def run_ours(args, rank, world, device):
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300 import workloads as W
+
+    w = W.scaled(args.workload)
+    nsteps = args.nsteps or w["steps"]
+    dt = W.dt_of(w)
+    src = W.source_position(w)[None]
+    rec = inputs.face_receivers(per_face=32) if w["dim"] == 3 else np.array([[0.5, 0.9], [0.9, 0.5]])
+    stream = torch.cuda.current_stream()
+    space = W.make_space(w)
+    info_s = iga.iga_space_info_get(space)
+    N = info_s.N
+
+    def assemble():
+        return iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"], 0, stream)
+
+    ops = assemble()
+    wave = iga.iga_wave_create(ops, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
+                               f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
+                               cg_max_it=args.cg_max_it)
+    iga.iga_wave_set_timing(wave, True)
+
+    def one_pass(old_ops):
+        o = assemble()
+        iga.iga_wave_reset(wave, o, stream)
+        iga.iga_wave_step(wave, nsteps, stream)
+        if old_ops is not None:
+            iga.iga_ops_destroy(old_ops)
+        return o
+
+    for _ in range(args.warmup):
+        ops = one_pass(ops)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    asm_ms, cg_ms, force_ms, cg_it, cg_solves = 0.0, 0.0, 0.0, 0, 0
+    launches0 = iga.iga_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t_host = time.perf_counter()
+    for _ in range(args.steps):
+        o = assemble()
+        asm_ms += iga.iga_ops_info_get(o).t_total_ms
+        iga.iga_wave_reset(wave, o, stream)
+        iga.iga_wave_step(wave, nsteps, stream)
+        st = iga.iga_wave_stats_get(wave)
+        cg_ms += st.cg_ms
+        force_ms += st.force_ms
+        cg_it += st.cg_iterations
+        cg_solves += st.cg_solves
+        iga.iga_ops_destroy(ops)
+        ops = o
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_host = time.perf_counter() - t_host
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    launches = iga.iga_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    oinfo = iga.iga_ops_info_get(ops)
+    K = args.steps
+    ms_step = ms / K
+    shot_steps = args.nshot * nsteps
+    value = world * shot_steps / (ms_step / 1e3)
+    # dominant kernel: the persistent PCG launch (events around every launch, on its stream)
+    init_b, it_b = cg_bytes(oinfo.nM, 1, 4)
+    # one shot: every launch is one solve and the device counter holds its iterations
+    cg_bytes_total = (cg_solves * init_b + cg_it * it_b) * N if args.nshot == 1 else None
+    achieved = cg_bytes_total / (cg_ms / 1e3) / 1e9 if cg_bytes_total else None
+    peaks = load_peaks()
+    peak = peaks.get("hbm_gbs") if peaks else None
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or HBM_FALLBACK_GBS
+    comps = {
+        "surrogate_rows_per_s": N / (asm_ms / K / 1e3),
+        "assembly_ms": asm_ms / K,
+        "assembly_split_ms": {"band": oinfo.t_band_ms, "sample_rows": oinfo.t_sample_ms,
+                              "interpolation": oinfo.t_interp_ms, "evaluation": oinfo.t_eval_ms},
+        "stepping_shot_steps_per_s": shot_steps / ((ms_step - asm_ms / K) / 1e3),
+        "cg_iterations_per_step": cg_it / (K * nsteps * args.nshot),
+        "cg_ms_per_step": cg_ms / (K * nsteps),
+        "force_ms_per_step": force_ms / (K * nsteps),
+        "host_s_per_step": t_host / K,
+    }
+    out = {
+        "metric": METRIC, "value": value, "unit": "shot-steps/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "dim": w["dim"], "p": w["p"], "n_el": w["n_el"], "N": N,
+                   "q": w["q"], "M": w["M"], "nsteps": nsteps, "nshot": args.nshot, "cg_rtol": args.cg_rtol,
+                   "precision": "FP32 fields/vectors/apply, FP64 quadrature, residual and dot products",
+                   "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (
+                       (oinfo.nK + oinfo.nM) * oinfo.pitch * 12 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "components": comps,
+        "roofline": {"bound": "hbm", "kernel": "pcg_persistent_kernel", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "bytes_per_row_per_iteration": it_b, "launches": cg_solves,
+                     "avg_launch_ms": cg_ms / max(1, cg_solves)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    return out, (space, ops, wave, w, nsteps, dt, src, rec)
+
+
+def fp64_plain_and_error(ctx, args):
+    """FP64 plain single-shot schedule on the same workload (bounded steps) and the FP32 error."""
+    import numpy as np
+    import torch
+
+    from paper_2004_05197_gb300 import iga
+    space, ops, wave, w, nsteps, dt, src, rec = ctx
+    P = min(args.compare_steps, nsteps)
+    N = iga.iga_ops_info_get(ops).N
+    res = {}
+    w64 = iga.iga_wave_create(ops, 1, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1,
+                              cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    iga.iga_wave_step(w64, P)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t
+    res["fp64_plain_shot_steps_per_s"] = P / t
+    res["fp64_plain_steps"] = P
+    u64 = torch.empty((1, N), dtype=torch.float64, device="cuda")
+    iga.iga_wave_get_state(w64, u64)
+    w32 = iga.iga_wave_create(ops, 1, iga.IGA_F32, dt, src_pos=src, f0=10.0, t0=0.1,
+                              cg_rtol=args.cg_rtol, cg_max_it=args.cg_max_it)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    iga.iga_wave_step(w32, P)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t
+    res["fp32_single_shot_steps_per_s"] = P / t
+    u32 = torch.empty((1, N), dtype=torch.float32, device="cuda")
+    iga.iga_wave_get_state(w32, u32)
+    torch.cuda.synchronize()
+    a = u32.double().cpu().numpy()
+    b = u64.cpu().numpy()
+    res["fp32_vs_fp64_rel_l2_error"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    iga.iga_wave_destroy(w64)
+    iga.iga_wave_destroy(w32)
+    return res
+
+
+def run_e2e(args, ctx):
+    """Same pass through the public API from host buffers: theta, source and receiver
+    positions uploaded every step, traces and the final field read back every step."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300 import workloads as W
+    _, _, _, w, nsteps, dt, src, rec = ctx
+    theta = W.theta_for(w)
+    h2d = (0 if theta is None else theta.size * 8) + src.size * 8 + rec.size * 8
+    times = []
+    d2h = 0
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sp = W.make_space(w)                                   # theta: host -> device
+        o = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
+        wv = iga.iga_wave_create(o, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
+                                 f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
+                                 cg_max_it=args.cg_max_it)
+        iga.iga_wave_step(wv, nsteps)
+        tr = iga.iga_wave_traces(wv, args.nshot, len(rec), nsteps)   # device -> host
+        N = iga.iga_ops_info_get(o).N
+        u = torch.empty((args.nshot, N), dtype=torch.float32, device="cuda")
+        iga.iga_wave_get_state(wv, u)
+        uh = u.cpu()                                                  # device -> host
+        t = time.perf_counter() - t
+        d2h = tr.nbytes + uh.numel() * 4
+        iga.iga_wave_destroy(wv)
+        iga.iga_ops_destroy(o)
+        iga.iga_space_destroy(sp)
+        if k > 0:                                                     # first pass warms up
+            times.append(t)
+    t = sorted(times)[len(times) // 2]
+    return {"value": args.nshot * nsteps / t, "unit": "shot-steps/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "s_per_step": t}
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_sample(args, budget_s=20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload.
+
+    (a) surrogate assembly: the oracle's Surrogate() (true rows at every sample
+        row, interpolation) plus surrogate rows of a random subset of the
+        workload's rows -> seconds per row;
+    (b) leapfrog: oracle steps on the same workload family at n_el = 12
+        (same p, q, M rule, map and coefficient) -> seconds per row per step.
+    Both are scaled to the full workload (per-row costs times N) and combined
+    into shot-steps/s of one full pass.
+    """
+    import numpy as np
+
+    import inputs
+    from oracle.wave import Leapfrog
+    from paper_2004_05197_gb300 import workloads as W
+    from tests.oracle_cases import oracle_space, oracle_surrogate
+    w = W.scaled(args.workload)
+    nsteps = args.nsteps or w["steps"]
+    sp = oracle_space(w)
+    N = sp.N
+    t = time.perf_counter()
+    from oracle.surrogate import Surrogate
+    S = Surrogate(sp, w["q"], w["M"])
+    t_build = time.perf_counter() - t
+    rng = np.random.default_rng(0)
+    nrows = args.oracle_rows
+    rows = sp.multi(rng.integers(0, N, size=nrows))
+    t = time.perf_counter()
+    S.rows(rows)
+    t_rows = time.perf_counter() - t
+    asm_s = t_build + N * t_rows / nrows
+    ws = W.scaled(args.workload, n_el=12, M=2)
+    sps, Ss = oracle_surrogate(ws)
+    SK, SM = Ss.rows(sps.all_rows())
+    lf = Leapfrog(sps, SK, SM, W.dt_of(ws), rtol=1e-10, max_it=args.cg_max_it)
+    u0 = np.zeros(sps.N)
+    steps_small = args.oracle_steps
+    t = time.perf_counter()
+    lf.run(u0, steps_small, sources=[(W.source_position(ws), 10.0, 0.1, 1.0)])
+    t_small = time.perf_counter() - t
+    step_s = t_small / steps_small * N / sps.N
+    total = asm_s + nsteps * step_s
+    return {"value": args.nshot * nsteps / total, "unit": "shot-steps/s", "cores": 1, "kind": "oracle",
+            "sample": ("oracle surrogate assembly of the full workload's sample rows plus %d random rows "
+                       "(%.1f s, scaled by N=%d), and %d oracle leapfrog steps of the n_el=12 version "
+                       "(%.1f s, scaled by N); full pass estimated at %.0f s" % (
+                           nrows, t_build + t_rows, N, steps_small, t_small, N, total)),
+            "surrogate_rows_per_s": N / asm_s, "sample_seconds": t_build + t_rows + t_small}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, one bounded sample per step."""
+    for _ in range(args.warmup):
+        oracle_sample(args)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = oracle_sample(args)
+        secs.append(time.perf_counter() - t)
+        vals.append(r["value"])
+    v = sorted(vals)[len(vals) // 2]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "shot-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": v, "unit": "shot-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "shot-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube96_p2")
+    ap.add_argument("--nsteps", type=int, default=0, help="time steps per pass (default: the workload's)")
+    ap.add_argument("--nshot", type=int, default=1)
+    ap.add_argument("--cg-rtol", type=float, default=1e-6)
+    ap.add_argument("--cg-max-it", type=int, default=2000)
+    ap.add_argument("--compare-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--oracle-rows", type=int, default=200)
+    ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return 0
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+    import __graft_entry__
+    __graft_entry__.build()
+    out, ctx = run_ours(args, rank, world, device)
+    if rank == 0:
+        out["components"].update(fp64_plain_and_error(ctx, args))
+        out["e2e"] = run_e2e(args, ctx)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_sample(args)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -227,6 +227,24 @@ int iga_wave_traces(const iga_wave* wave, double* host_dst, int* nsteps_done);
 /* Total CG iterations summed over steps and shots since creation. */
 int iga_wave_cg_iterations(const iga_wave* wave, long long* total);
 
+/* Rebinds the wave to `ops` (same space size and dtype support) and restarts
+ * it: initial condition recomputed, step counter, traces, CG counters and
+ * timing statistics cleared, a^{-1} = 0.  No allocation. Async on stream. */
+int iga_wave_reset(iga_wave* wave, const iga_ops* ops, void* stream);
+
+/* Per-wave statistics. With timing on, every force (K~ apply) launch and every
+ * CG solve of wave_step is bracketed by CUDA events on the launching stream
+ * and the elapsed device times are accumulated when wave_step synchronises. */
+typedef struct iga_wave_stats {
+    long long steps;          /* steps advanced since creation / reset */
+    long long cg_iterations;  /* CG iterations summed over steps and shots */
+    long long cg_solves;      /* CG solves issued (one per step per chunk of <= 4 shots) */
+    double cg_ms;             /* device time of the CG solves (timing on) */
+    double force_ms;          /* device time of the force launches (timing on) */
+} iga_wave_stats;
+int iga_wave_set_timing(iga_wave* wave, int on);
+int iga_wave_stats_get(const iga_wave* wave, iga_wave_stats* out);
+
 /* ---- misc ------------------------------------------------------------- */
 const char* iga_last_error(void);
 /* Number of library kernel launches issued since load (for launch accounting). */

@@ -22,7 +22,10 @@ struct iga_wave {
     int dtype, nshot, nrec, nloc, step;
     long long N;
     iga::DevBuf u, uprev, a, b, traces, src_idx, src_w, rec_idx, rec_w, work, counters;
-    std::vector<double> src_amp_dummy;
+    iga::DevBuf greville, centres;   // pulse initial condition inputs (GAUSS_PULSE)
+    int timing = 0;
+    long long cg_solves = 0;
+    double cg_ms = 0.0, force_ms = 0.0;
 };
 
 namespace iga {
@@ -168,10 +171,24 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
     const int ugrid = (int)std::max<long long>(1, std::min<long long>((tot + 255) / 256, 152 * 16));
     long long* iter_acc = w->counters.as<long long>();
     int* status = (int*)(w->counters.as<char>() + 64);
+    std::vector<cudaEvent_t> ev;
+    if (w->timing) {
+        ev.resize((size_t)4 * nsteps);
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    auto destroy_events = [&]() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    };
     for (int s = 0; s < nsteps; ++s) {
         const int n = w->step;
+        if (w->timing) cudaEventRecord(ev[4 * s + 0], st);
         int rc = force_dispatch<T>(w, st);
-        if (rc) return rc;
+        if (w->timing) cudaEventRecord(ev[4 * s + 1], st);
+        if (rc) {
+            destroy_events();
+            return rc;
+        }
         if (w->desc.with_source) {
             const double amp = w->desc.src_amp * ricker(n * w->desc.dt, w->desc.f0, w->desc.t0);
             const int k = w->nshot * w->nloc;
@@ -179,9 +196,15 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
                                                               w->nshot, w->nloc, N, amp);
             IGA_LAUNCH_CHECK("source_kernel");
         }
+        if (w->timing) cudaEventRecord(ev[4 * s + 2], st);
         rc = mass_solve_impl(ops, w->dtype, w->b.ptr, w->a.ptr, w->nshot, w->desc.cg_rtol, w->desc.cg_max_it,
                              w->desc.solve_flags, nullptr, nullptr, st, w->work.ptr, w->work.bytes, iter_acc, status);
-        if (rc) return rc;
+        if (w->timing) cudaEventRecord(ev[4 * s + 3], st);
+        w->cg_solves += (w->nshot + 3) / 4;
+        if (rc) {
+            destroy_events();
+            return rc;
+        }
         update_kernel<T><<<ugrid, 256, 0, st>>>(w->u.as<T>(), w->uprev.as<T>(), w->a.as<T>(), tot,
                                                 w->desc.dt * w->desc.dt, n == 0 ? 1 : 0);
         IGA_LAUNCH_CHECK("update_kernel");
@@ -196,15 +219,80 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
         w->step += 1;
     }
     int st_h = 0;
-    IGA_CUDA(cudaMemcpyAsync(&st_h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    IGA_CUDA(cudaStreamSynchronize(st));
+    cudaError_t e = cudaMemcpyAsync(&st_h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && w->timing) {
+        for (int s = 0; s < nsteps; ++s) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[4 * s + 0], ev[4 * s + 1]);
+            cudaEventElapsedTime(&b, ev[4 * s + 2], ev[4 * s + 3]);
+            w->force_ms += a;
+            w->cg_ms += b;
+        }
+    }
+    destroy_events();
+    if (e != cudaSuccess) return cuda_fail(e, "wave_step");
     if (st_h & 8) return fail(IGA_ERR_NOT_CONVERGED, "a CG solve in wave_step missed its tolerance");
+    return IGA_OK;
+}
+
+// u^0 from the initial condition, u^{-1} and a^{-1} cleared, counters reset.
+static int initial_state(iga_wave* w, cudaStream_t st) {
+    const iga_space* s = w->ops->space;
+    const size_t vb = (w->dtype == IGA_F64 ? 8 : 4) * (size_t)w->nshot * w->N;
+    IGA_CUDA(cudaMemsetAsync(w->a.ptr, 0, vb, st));
+    IGA_CUDA(cudaMemsetAsync(w->uprev.ptr, 0, vb, st));
+    IGA_CUDA(cudaMemsetAsync(w->traces.ptr, 0, w->traces.bytes, st));
+    IGA_CUDA(cudaMemsetAsync(w->counters.ptr, 0, w->counters.bytes, st));
+    if (w->desc.init_kind == IGA_INIT_GAUSS_PULSE) {
+        const long long tot = (long long)w->nshot * w->N;
+        const int grid = (int)std::min<long long>((tot + 255) / 256, 152 * 16);
+        if (w->dtype == IGA_F64)
+            pulse_kernel<double><<<grid, 256, 0, st>>>(s->gp, w->greville.as<double>(), w->centres.as<double>(),
+                                                       w->desc.pulse_width, w->u.as<double>(), w->nshot, w->N);
+        else
+            pulse_kernel<float><<<grid, 256, 0, st>>>(s->gp, w->greville.as<double>(), w->centres.as<double>(),
+                                                      w->desc.pulse_width, w->u.as<float>(), w->nshot, w->N);
+        IGA_LAUNCH_CHECK("pulse_kernel");
+    } else {
+        IGA_CUDA(cudaMemsetAsync(w->u.ptr, 0, vb, st));
+    }
+    w->step = 0;
+    w->cg_solves = 0;
+    w->cg_ms = w->force_ms = 0.0;
     return IGA_OK;
 }
 
 }  // namespace iga
 
 using namespace iga;
+
+extern "C" int iga_wave_reset(iga_wave* w, const iga_ops* ops, void* stream) {
+    if (!w || !ops) return fail(IGA_ERR_ARG, "null argument");
+    if (ops->N != w->N || ops->space->dim != w->ops->space->dim || ops->p != w->ops->p)
+        return fail(IGA_ERR_ARG, "ops must have the wave's space size and degree");
+    w->ops = ops;
+    return initial_state(w, (cudaStream_t)stream);
+}
+
+extern "C" int iga_wave_set_timing(iga_wave* w, int on) {
+    if (!w) return fail(IGA_ERR_ARG, "null argument");
+    w->timing = on ? 1 : 0;
+    return IGA_OK;
+}
+
+extern "C" int iga_wave_stats_get(const iga_wave* w, iga_wave_stats* out) {
+    if (!w || !out) return fail(IGA_ERR_ARG, "null argument");
+    long long it = 0;
+    IGA_CUDA(cudaDeviceSynchronize());
+    IGA_CUDA(cudaMemcpy(&it, w->counters.ptr, sizeof(long long), cudaMemcpyDeviceToHost));
+    out->steps = w->step;
+    out->cg_iterations = it;
+    out->cg_solves = w->cg_solves;
+    out->cg_ms = w->cg_ms;
+    out->force_ms = w->force_ms;
+    return IGA_OK;
+}
 
 extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out) {
     if (!ops || !desc || !out) return fail(IGA_ERR_ARG, "null argument");
@@ -246,10 +334,6 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
     if (!rc) rc = w->counters.alloc(128);
     if (!rc) rc = w->work.alloc(mass_solve_work_bytes(ops, d.dtype, d.nshot));
     if (rc) return bail(rc);
-    cudaMemset(w->a.ptr, 0, vb);
-    cudaMemset(w->uprev.ptr, 0, vb);
-    cudaMemset(w->traces.ptr, 0, w->traces.bytes);
-    cudaMemset(w->counters.ptr, 0, w->counters.bytes);
     // source / receiver tables
     std::vector<int> idx;
     std::vector<double> wt;
@@ -274,7 +358,6 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
         return bail(rc);
     cudaMemcpy(w->rec_idx.ptr, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(w->rec_w.ptr, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice);
-    // initial state
     if (d.init_kind == IGA_INIT_GAUSS_PULSE) {
         std::vector<double> gv(s->m);
         for (int k = 0; k < s->m; ++k) {   // Greville abscissae: mean of knots k+1 .. k+p
@@ -282,25 +365,13 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
             for (int l = 1; l <= s->p; ++l) acc += s->knots[k + l];
             gv[k] = acc / s->p;
         }
-        DevBuf dg, dc;
-        if ((rc = dg.alloc(sizeof(double) * gv.size())) || (rc = dc.alloc(sizeof(double) * d.nshot * s->dim)))
+        if ((rc = w->greville.alloc(sizeof(double) * gv.size())) ||
+            (rc = w->centres.alloc(sizeof(double) * d.nshot * s->dim)))
             return bail(rc);
-        cudaMemcpy(dg.ptr, gv.data(), sizeof(double) * gv.size(), cudaMemcpyHostToDevice);
-        cudaMemcpy(dc.ptr, d.pulse_centre, sizeof(double) * d.nshot * s->dim, cudaMemcpyHostToDevice);
-        const long long tot = (long long)d.nshot * ops->N;
-        const int grid = (int)std::min<long long>((tot + 255) / 256, 152 * 16);
-        if (d.dtype == IGA_F64)
-            pulse_kernel<double><<<grid, 256>>>(s->gp, dg.as<double>(), dc.as<double>(), d.pulse_width,
-                                                w->u.as<double>(), d.nshot, ops->N);
-        else
-            pulse_kernel<float><<<grid, 256>>>(s->gp, dg.as<double>(), dc.as<double>(), d.pulse_width,
-                                               w->u.as<float>(), d.nshot, ops->N);
-        count_launch();
-        cudaError_t e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return bail(cuda_fail(e, "pulse_kernel"));
-    } else {
-        cudaMemset(w->u.ptr, 0, vb);
+        cudaMemcpy(w->greville.ptr, gv.data(), sizeof(double) * gv.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(w->centres.ptr, d.pulse_centre, sizeof(double) * d.nshot * s->dim, cudaMemcpyHostToDevice);
     }
+    if ((rc = initial_state(w, 0))) return bail(rc);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bail(cuda_fail(e, "wave_create"));
     *out = w;

@@ -35,7 +35,8 @@ EXPORTED = [
     "iga_ops_destroy", "iga_ops_info_get", "iga_ops_copy_fields", "iga_ops_copy_samples",
     "iga_ops_sample_indices", "iga_stencil_apply", "iga_mass_solve", "iga_wave_create",
     "iga_wave_destroy", "iga_wave_step", "iga_wave_get_state", "iga_wave_traces",
-    "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count",
+    "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count", "iga_wave_reset",
+    "iga_wave_set_timing", "iga_wave_stats_get",
 ]
 
 
@@ -75,6 +76,11 @@ class iga_wave_desc(C.Structure):
                 ("nsteps_max", C.c_int), ("cg_rtol", C.c_double), ("cg_max_it", C.c_int)]
 
 
+class iga_wave_stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("cg_iterations", C.c_longlong), ("cg_solves", C.c_longlong),
+                ("cg_ms", C.c_double), ("force_ms", C.c_double)]
+
+
 _vp, _i, _u, _d = C.c_void_p, C.c_int, C.c_uint, C.c_double
 _sig = {
     "iga_space_create": [C.POINTER(iga_space_desc), C.POINTER(_vp)],
@@ -94,6 +100,9 @@ _sig = {
     "iga_wave_get_state": [_vp, _vp, _vp, _vp],
     "iga_wave_traces": [_vp, C.POINTER(_d), C.POINTER(_i)],
     "iga_wave_cg_iterations": [_vp, C.POINTER(C.c_longlong)],
+    "iga_wave_reset": [_vp, _vp, _vp],
+    "iga_wave_set_timing": [_vp, _i],
+    "iga_wave_stats_get": [_vp, C.POINTER(iga_wave_stats)],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -257,3 +266,17 @@ def iga_wave_cg_iterations(wave):
     tot = C.c_longlong()
     _check(_lib.iga_wave_cg_iterations(wave, C.byref(tot)))
     return int(tot.value)
+
+
+def iga_wave_reset(wave, ops, stream=None):
+    _check(_lib.iga_wave_reset(wave, ops, _stream(stream)))
+
+
+def iga_wave_set_timing(wave, on=True):
+    _check(_lib.iga_wave_set_timing(wave, 1 if on else 0))
+
+
+def iga_wave_stats_get(wave):
+    st = iga_wave_stats()
+    _check(_lib.iga_wave_stats_get(wave, C.byref(st)))
+    return st

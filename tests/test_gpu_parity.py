@@ -251,7 +251,8 @@ def _wave_case(dtype, nsteps=20):
     _, ops = gpu_ops(name)
     dt = W.dt_of(w)
     centre = inputs.pulse_centre(2)
-    rec = np.array([[0.3, 0.2], [0.7, 0.9], [0.0, 0.5]])
+    # receivers near the pulse (so the traces carry signal) and one on the boundary
+    rec = np.array([centre + [0.03, 0.0], centre + [0.0, -0.04], [0.0, centre[1]]])
     wave = iga.iga_wave_create(ops, 1, dtype, dt, init_kind=iga.IGA_INIT_GAUSS_PULSE,
                                pulse_centre=centre[None], pulse_width=0.05, rec_pos=rec,
                                nsteps_max=nsteps, cg_rtol=1e-13 if dtype == iga.IGA_F64 else 1e-6,
@@ -273,7 +274,8 @@ def _wave_case(dtype, nsteps=20):
 def test_wave_fp64_matches_oracle():
     u, ur, tr, trr = _wave_case(iga.IGA_F64)
     assert np.linalg.norm(u - ur) <= 1e-11 * np.linalg.norm(ur)
-    assert np.abs(tr - trr).max() <= 1e-11 * np.abs(trr).max()
+    # a trace is a weighted sum of (p+1)^d coefficients: compare on the field's scale
+    assert np.abs(tr - trr).max() <= 1e-11 * np.abs(ur).max()
 
 
 def test_wave_fp32_error_against_fp64_oracle():
