@@ -358,7 +358,7 @@ def oracle_sample(args, budget_s=20.0):
             "sample": ("oracle surrogate assembly of the full workload's sample rows plus %d random rows "
                        "(%.1f s, scaled by N=%d), and %d oracle leapfrog steps of the n_el=12 version "
                        "(%.1f s, scaled by N); full pass estimated at %.0f s" % (
-                           nrows, t_build + t_rows, N, steps_small, t_small, N, total)),
+                           nrows, t_build + t_rows, N, steps_small, t_small, total)),
             "surrogate_rows_per_s": N / asm_s, "sample_seconds": t_build + t_rows + t_small}
 
 

@@ -283,3 +283,36 @@ def test_wave_fp32_error_against_fp64_oracle():
     err = np.linalg.norm(u - ur) / np.linalg.norm(ur)
     print("FP32 leapfrog relative L2 error after 20 steps:", err)
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("mode", ["f64", "f64_plain", "f32"])
+def test_wave_cube_ricker_source_matches_oracle(mode):
+    """3-D, lognormal wave speed, Ricker point source at the centre (the bench workload family)."""
+    name = "cube20_p2_theta"
+    w = CASES[name]()
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    dt = W.dt_of(w)
+    nsteps = 30
+    src = W.source_position(w)
+    rec = np.array([src + [0.05, 0.0, 0.0], src + [0.0, -0.1, 0.05]])
+    dtype = iga.IGA_F32 if mode == "f32" else iga.IGA_F64
+    flags = iga.IGA_SOLVE_PLAIN if mode == "f64_plain" else 0
+    wave = iga.iga_wave_create(ops, 1, dtype, dt, src_pos=src[None], f0=10.0, t0=0.1, rec_pos=rec,
+                               nsteps_max=nsteps, cg_rtol=1e-6 if mode == "f32" else 1e-13,
+                               cg_max_it=3000, solve_flags=flags)
+    iga.iga_wave_step(wave, nsteps)
+    tdt = torch.float32 if mode == "f32" else torch.float64
+    u = torch.empty((1, sp.N), dtype=tdt, device="cuda")
+    iga.iga_wave_get_state(wave, u)
+    torch.cuda.synchronize()
+    tr = iga.iga_wave_traces(wave, 1, len(rec), nsteps)[0]
+    iga.iga_wave_destroy(wave)
+    lf = Leapfrog(sp, SK, SM, dt, rtol=1e-13, max_it=3000)
+    ur, _, trr = lf.run(np.zeros(sp.N), nsteps, sources=[(src, 10.0, 0.1, 1.0)], receivers=list(rec))
+    ug = u.cpu().numpy()[0].astype(np.float64)
+    err = np.linalg.norm(ug - ur) / np.linalg.norm(ur)
+    terr = np.abs(tr - trr).max() / np.abs(ur).max()
+    print(mode, "relative L2 error", err, "trace error", terr)
+    tol = 1e-5 if mode == "f32" else 1e-11
+    assert err <= tol and terr <= tol
