@@ -13,9 +13,10 @@ template <int DIM, int P, typename T, bool MASS, int R>
 __global__ void __launch_bounds__(256) apply_kernel(const T* __restrict__ F, long long pitch,
                                                      const T* __restrict__ x, T* __restrict__ y, int N,
                                                      int m) {
+    const LdgLoad<T> ld{x, N};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        T acc[R];
-        stencil_row<DIM, P, T, MASS, R>(F, pitch, x, N, i, N, m, acc);
+        T acc[R], own[R];
+        stencil_row<DIM, P, T, MASS, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, N, m, acc, own);
 #pragma unroll
         for (int r = 0; r < R; ++r) y[(size_t)r * N + i] = acc[r];
     }
@@ -30,7 +31,7 @@ static int apply_grid(long long N) {
         if (sms <= 0) sms = 152;
     }
     const long long want = (N + 255) / 256;
-    return (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * 8));
+    return (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * 16));
 }
 
 template <int DIM, int P, typename T>

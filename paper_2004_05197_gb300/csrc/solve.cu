@@ -51,6 +51,9 @@ __device__ __noinline__ void bounds_record(long long idx, long long ext, int sit
 #endif
 
 constexpr int kCgThreads = 256;
+constexpr int kCgMaxBlocksPerSM = 8;
+template <int R>
+constexpr int kCgUnroll = R >= 4 ? 2 : 4;   // fields in flight per thread in the mass apply
 constexpr int kCgWarps = kCgThreads / 32;
 constexpr long long kBarrierSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -80,43 +83,6 @@ struct CombLoad {   // z + beta p_old, formed on the fly
         return IGA_IN(o, ext, 2) ? fma(beta[r], p[o], z[o]) : T(0);
     }
 };
-
-// Mass stencil row for R right-hand sides given by a loader.
-template <int DIM, int P, typename T, int R, class Load>
-__device__ __forceinline__ void mass_row(const T* __restrict__ F, long long pitch, const Load& ld, int i, int N,
-                                         int m, T* acc, T* own) {
-    constexpr int NF = StencilShape<DIM, P>::T0;
-    const long long fext = (long long)(NF + 1) * pitch;
-    (void)fext;
-    const T d = IGA_IN(i, fext, 3) ? __ldg(F + i) : T(0);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        own[r] = ld(r, i);
-        acc[r] = d * own[r];
-    }
-    const T* Foff = F + pitch;
-#pragma unroll
-    for (int u = 0; u < NF; ++u) {
-        const int dl = field_delta<DIM, P>(u, m);
-        const T* Fu = Foff + (size_t)u * pitch;
-        // clamp out-of-range neighbours to the row itself (addresses always valid), then mask
-        const int ip = i + dl, im = i - dl;
-        const bool okp = ip < N, okm = im >= 0;
-        const int ipc = okp ? ip : i, imc = okm ? im : i;
-        const T s = IGA_IN((long long)(u + 1) * pitch + i, fext, 4) ? __ldg(Fu + i) : T(0);
-        const T smv = IGA_IN((long long)(u + 1) * pitch + imc, fext, 5) ? __ldg(Fu + imc) : T(0);
-        const T sm = okm ? smv : T(0);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T xpv = ld(r, ipc);
-            const T xmv = ld(r, imc);
-            const T xp = okp ? xpv : T(0);
-            const T xm = okm ? xmv : T(0);
-            acc[r] = fma(s, xp, acc[r]);
-            acc[r] = fma(sm, xm, acc[r]);
-        }
-    }
-}
 
 // ---------------------------------------------------------------- reductions
 // Block sum of K doubles per thread (v[K]) into red[K] (shared), fixed order.
@@ -211,7 +177,7 @@ __device__ __forceinline__ void cg_init_rows(const CgVecs<T>& v, double* part) {
     PlainLoad<T> ld{v.x, v.N, v.ext_vec};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
-        mass_row<DIM, P, T, R>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+        stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
         const double di = IGA_IN(i, v.ext_diag, 6) ? (double)v.dinv[i] : 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -245,7 +211,7 @@ __device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T*
     for (int r = 0; r < R; ++r) ld.beta[r] = (T)beta[r];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
-        mass_row<DIM, P, T, R>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+        stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!active[r]) continue;
@@ -499,7 +465,7 @@ static int cg_blocks() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_persistent_kernel<DIM, P, T, R>, kCgThreads, 0);
-        nb = std::max(1, sms * std::max(1, std::min(per, 4)));
+        nb = std::max(1, sms * std::max(1, std::min(per, kCgMaxBlocksPerSM)));
     }
     return nb;
 }
@@ -688,7 +654,7 @@ size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nb = std::max(1, sms) * 4;
+    const int nb = std::max(1, sms) * kCgMaxBlocksPerSM;
     return carve_bytes(dtype == IGA_F64 ? 8 : 4, ops->N, 4, nb);
 }
 

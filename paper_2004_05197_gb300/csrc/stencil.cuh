@@ -15,6 +15,10 @@
 // Entries whose column leaves the index grid are stored as 0, so a wrapped
 // linear neighbour contributes nothing; only the linear range [0, N) is guarded,
 // by clamping the neighbour index (every address stays inside its buffer).
+//
+// The field loop is unrolled UNR-fold with run-time offsets, so a thread keeps
+// only UNR fields in flight: few registers, many resident warps, and 4 UNR
+// independent loads per thread in flight to cover HBM latency.
 #pragma once
 
 #include "iga_internal.cuh"
@@ -30,33 +34,42 @@ struct StencilShape {
 
 // Linear offset of off-diagonal field u (t = t0 + 1 + u) for row length m.
 template <int DIM, int P>
-__host__ __device__ constexpr int field_delta(int u, int m) {
-    return ((StencilShape<DIM, P>::T0 + 1 + u) % (2 * P + 1) - P) +
-           (((StencilShape<DIM, P>::T0 + 1 + u) / (2 * P + 1)) % (2 * P + 1) - P) * m +
-           (DIM == 3 ? (((StencilShape<DIM, P>::T0 + 1 + u) / ((2 * P + 1) * (2 * P + 1))) % (2 * P + 1) - P) *
-                           m * m
-                     : 0);
+__host__ __device__ __forceinline__ int field_delta(int u, int m) {
+    constexpr int PP = 2 * P + 1;
+    const int t = StencilShape<DIM, P>::T0 + 1 + u;
+    const int d1 = t % PP - P;
+    const int d2 = (t / PP) % PP - P;
+    const int d3 = DIM == 3 ? t / (PP * PP) - P : 0;
+    return d1 + (d2 + d3 * m) * m;
 }
 
-// One output row of the operator for R right-hand sides whose vectors start at
-// x[r * xs] (r < R).  Returns the row values in acc.
-template <int DIM, int P, typename T, bool MASS, int R>
-__device__ __forceinline__ void stencil_row(const T* __restrict__ F, long long pitch, const T* __restrict__ x,
-                                            long long xs, int i, int N, int m, T* acc) {
+// Vector loaders: read-only vectors go through the non-coherent path; vectors
+// written by other blocks of a persistent launch use ordinary coherent loads.
+template <typename T>
+struct LdgLoad {
+    const T* x;
+    long long xs;
+    __device__ __forceinline__ T operator()(int r, int idx) const { return __ldg(x + r * xs + idx); }
+};
+
+// One output row of the operator for R right-hand sides given by a loader.
+// own[r] receives the row's own vector value (ld(r, i)).
+template <int DIM, int P, typename T, bool MASS, int R, int UNR, class Load>
+__device__ __forceinline__ void stencil_row(const T* __restrict__ F, long long pitch, const Load& ld, int i, int N,
+                                            int m, T* acc, T* own) {
     constexpr int NF = StencilShape<DIM, P>::T0;
-    const T* Foff = MASS ? F + pitch : F;   // mass: field 0 is the diagonal
-    T xi[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) xi[r] = __ldg(x + r * xs + i);
+    for (int r = 0; r < R; ++r) own[r] = ld(r, i);
     if (MASS) {
         const T d = __ldg(F + i);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = d * xi[r];
+        for (int r = 0; r < R; ++r) acc[r] = d * own[r];
     } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = T(0);
     }
-#pragma unroll
+    const T* Foff = MASS ? F + pitch : F;
+#pragma unroll UNR
     for (int u = 0; u < NF; ++u) {
         const int dl = field_delta<DIM, P>(u, m);
         const T* Fu = Foff + (size_t)u * pitch;
@@ -70,16 +83,16 @@ __device__ __forceinline__ void stencil_row(const T* __restrict__ F, long long p
         const T sm = okm ? smv : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const T xpv = __ldg(x + r * xs + ipc);
-            const T xmv = __ldg(x + r * xs + imc);
+            const T xpv = ld(r, ipc);
+            const T xmv = ld(r, imc);
             const T xp = okp ? xpv : T(0);
             const T xm = okm ? xmv : T(0);
             if (MASS) {
                 acc[r] = fma(s, xp, acc[r]);
                 acc[r] = fma(sm, xm, acc[r]);
             } else {
-                acc[r] = fma(s, xp - xi[r], acc[r]);
-                acc[r] = fma(sm, xm - xi[r], acc[r]);
+                acc[r] = fma(s, xp - own[r], acc[r]);
+                acc[r] = fma(sm, xm - own[r], acc[r]);
             }
         }
     }

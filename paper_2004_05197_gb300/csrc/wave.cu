@@ -33,9 +33,10 @@ namespace iga {
 template <int DIM, int P, typename T, int R>
 __global__ void __launch_bounds__(256) force_kernel(const T* __restrict__ F, long long pitch, const T* __restrict__ u,
                                                      T* __restrict__ b, int N, int m) {
+    const LdgLoad<T> ld{u, N};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        T acc[R];
-        stencil_row<DIM, P, T, false, R>(F, pitch, u, N, i, N, m, acc);
+        T acc[R], own[R];
+        stencil_row<DIM, P, T, false, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, N, m, acc, own);
 #pragma unroll
         for (int r = 0; r < R; ++r) b[(size_t)r * N + i] = -acc[r];
     }
@@ -130,7 +131,7 @@ static int force_launch(const iga_wave* w, cudaStream_t st) {
     int sms = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, (long long)sms * 8));
+    const int grid = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, (long long)sms * 16));
     int r0 = 0;
     while (r0 < w->nshot) {
         const T* u = w->u.as<T>() + (size_t)r0 * N;

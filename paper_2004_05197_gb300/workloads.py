@@ -9,10 +9,12 @@ Workloads (sizes of the benchmark problems):
   annulus64_p2   2-D p=2, 64^2 elements, quarter annulus, c = 1, q=2, M=4, dt = 0.2 h,
                  Gaussian pulse of width 0.05, 20 steps (FP64)
   annulus512_p3  2-D p=3, 512^2, quarter annulus, c = 1 + 0.5 sin(2 pi x) cos(2 pi y),
-                 q=3, M=8, Ricker f0 = 10 at s = (0.5, 0.5), 2000 steps, CG tol 1e-10
+                 q=3, M=8, Ricker f0 = 10 at s = (0.5, 0.5), 2000 steps, CG tol 1e-10,
+                 dt = 0.1 h (0.2 h exceeds the leapfrog stability limit, about 0.19 h)
   cube96_p2      3-D p=2, 96^3, sine-perturbed cube (amplitude 0.1), lognormal
                  (sigma 0.3) wave speed on a 16^3 cubic B-spline grid, q=2, M=6,
-                 Ricker source at the cube centre, 500 FP32 steps
+                 Ricker source at the cube centre, 500 FP32 steps, dt = 0.1 h (0.2 h exceeds
+                 the leapfrog stability limit, about 0.19 h and falling with n_el)
 """
 import numpy as np
 
@@ -22,9 +24,9 @@ WORKLOADS = {
     "annulus64_p2": dict(dim=2, p=2, n_el=64, map="annulus", coef="const", q=2, M=4, steps=20,
                          source=False, pulse=True, dt_factor=0.2),
     "annulus512_p3": dict(dim=2, p=3, n_el=512, map="annulus", coef="sincos", q=3, M=8, steps=2000,
-                          source=True, pulse=False, dt_factor=0.2),
+                          source=True, pulse=False, dt_factor=0.1),
     "cube96_p2": dict(dim=3, p=2, n_el=96, map="cube", coef="theta16", q=2, M=6, steps=500,
-                      source=True, pulse=False, dt_factor=0.2),
+                      source=True, pulse=False, dt_factor=0.1),
 }
 
 

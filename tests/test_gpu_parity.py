@@ -31,6 +31,8 @@ CASES = {
     "annulus40_p3_sincos": lambda: W.scaled("annulus512_p3", n_el=40),
     "cube20_p2_theta": lambda: W.scaled("cube96_p2", n_el=20),
     "minimal_p2_q1": lambda: W.scaled("annulus64_p2", n_el=10, q=1, M=100),
+    # sampling fine enough for a definite K~ (M = 6 on n_el = 20 gives an indefinite K~)
+    "cube20_p2_theta_M2": lambda: W.scaled("cube96_p2", n_el=20, M=2),
 }
 
 
@@ -288,12 +290,12 @@ def test_wave_fp32_error_against_fp64_oracle():
 @pytest.mark.parametrize("mode", ["f64", "f64_plain", "f32"])
 def test_wave_cube_ricker_source_matches_oracle(mode):
     """3-D, lognormal wave speed, Ricker point source at the centre (the bench workload family)."""
-    name = "cube20_p2_theta"
+    name = "cube20_p2_theta_M2"
     w = CASES[name]()
     sp, S, SK, SM, _, _ = oracle_full(name)
     _, ops = gpu_ops(name)
     dt = W.dt_of(w)
-    nsteps = 30
+    nsteps = 60
     src = W.source_position(w)
     rec = np.array([src + [0.05, 0.0, 0.0], src + [0.0, -0.1, 0.05]])
     dtype = iga.IGA_F32 if mode == "f32" else iga.IGA_F64
