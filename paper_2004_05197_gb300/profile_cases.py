@@ -1,0 +1,33 @@
+"""Small profiling cases for ncu: K~ applies and a short fixed-iteration PCG solve.
+
+    python -m paper_2004_05197_gb300.profile_cases [n_el]
+
+Workload: the cube96_p2 family at n_el (default 80: the FP32 fields exceed L2).
+"""
+import sys
+
+import torch
+
+import inputs
+from paper_2004_05197_gb300 import iga
+from paper_2004_05197_gb300 import workloads as W
+
+
+def main(n_el=80):
+    w = W.scaled("cube96_p2", n_el=n_el)
+    sp = W.make_space(w)
+    ops = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
+    N = iga.iga_ops_info_get(ops).N
+    x = torch.tensor(inputs.vectors(N, 1), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(2):
+        iga.iga_stencil_apply(ops, iga.IGA_OP_K, iga.IGA_F32, x, y, 1)
+    for _ in range(2):
+        a = torch.zeros_like(x)
+        iga.iga_mass_solve(ops, iga.IGA_F32, x, a, 1, 0.0, 10)
+    torch.cuda.synchronize()
+    print("ok N", N)
+
+
+if __name__ == "__main__":
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 80)
