@@ -186,6 +186,15 @@ int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nr
                    double rtol, int max_it, unsigned flags, int* iters_out,
                    double* relres_out, void* stream);
 
+/* ---- spectrum --------------------------------------------------------------
+ * Extreme eigenvalues of the pencil K~ v = lambda M~ v by k Lanczos steps in the
+ * M~ inner product (each step: one K~ apply, one mass solve, one M~ apply).
+ * The leapfrog step is stable iff dt sqrt(lambda_max) < 2 (no CFL is given in
+ * the paper); lambda_min < 0 reports an indefinite surrogate K~ (sampling
+ * length too large for the coefficient).  Synchronous (host scalars). */
+int iga_ops_spectrum(const iga_ops* ops, int dtype, int k, double* lambda_min, double* lambda_max,
+                     void* stream);
+
 /* ---- wave time stepping ------------------------------------------------
  * Leapfrog for M~ u'' + K~ u = f (unit density, natural boundary
  * conditions): a^n solves M~ a^n = f^n - K~ u^n by Jacobi-PCG started from
@@ -210,6 +219,8 @@ typedef struct iga_wave_desc {
     int nsteps_max;             /* capacity of the trace buffer (steps) */
     double cg_rtol;
     int cg_max_it;
+    int cfl_check;              /* 1: estimate lambda_max(M~^-1 K~) by Lanczos at create / reset and
+                                   refuse (IGA_ERR_ARG) steps with dt sqrt(lambda_max) >= 2 */
 } iga_wave_desc;
 
 int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);
@@ -241,6 +252,8 @@ typedef struct iga_wave_stats {
     long long cg_solves;      /* CG solves issued (one per step per chunk of <= 4 shots) */
     double cg_ms;             /* device time of the CG solves (timing on) */
     double force_ms;          /* device time of the force launches (timing on) */
+    double lambda_min;        /* Lanczos estimates of the pencil (K~, M~) (cfl_check on, else 0) */
+    double lambda_max;
 } iga_wave_stats;
 int iga_wave_set_timing(iga_wave* wave, int on);
 int iga_wave_stats_get(const iga_wave* wave, iga_wave_stats* out);

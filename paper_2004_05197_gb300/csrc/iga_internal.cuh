@@ -98,6 +98,7 @@ int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, int n
                     int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st,
                     void* work, size_t work_bytes, long long* iter_acc, int* status_acc);
 size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs);
+int spectrum_impl(const iga_ops* ops, int dtype, int k, double* lam_min, double* lam_max, cudaStream_t st);
 // colex decode of stencil offset t into delta (0..dim-1), values in [-p, p]
 inline void decode_offset(int t, int dim, int p, int delta[3]) {
     int P = 2 * p + 1;

@@ -26,6 +26,7 @@ struct iga_wave {
     int timing = 0;
     long long cg_solves = 0;
     double cg_ms = 0.0, force_ms = 0.0;
+    double lam_min = 0.0, lam_max = 0.0;
 };
 
 namespace iga {
@@ -261,6 +262,10 @@ static int initial_state(iga_wave* w, cudaStream_t st) {
     w->step = 0;
     w->cg_solves = 0;
     w->cg_ms = w->force_ms = 0.0;
+    if (w->desc.cfl_check) {
+        int rc = spectrum_impl(w->ops, IGA_F32, 40, &w->lam_min, &w->lam_max, st);
+        if (rc) return rc;
+    }
     return IGA_OK;
 }
 
@@ -292,6 +297,8 @@ extern "C" int iga_wave_stats_get(const iga_wave* w, iga_wave_stats* out) {
     out->cg_solves = w->cg_solves;
     out->cg_ms = w->cg_ms;
     out->force_ms = w->force_ms;
+    out->lambda_min = w->lam_min;
+    out->lambda_max = w->lam_max;
     return IGA_OK;
 }
 
@@ -389,6 +396,8 @@ extern "C" int iga_wave_step(iga_wave* w, int nsteps, void* stream) {
     if (nsteps < 0) return fail(IGA_ERR_ARG, "nsteps must be >= 0");
     if (w->nrec > 0 && w->step + nsteps > w->desc.nsteps_max) return fail(IGA_ERR_ARG, "trace buffer would overflow");
     if (nsteps == 0) return IGA_OK;
+    if (w->desc.cfl_check && w->desc.dt * std::sqrt(1.02 * w->lam_max) >= 2.0)
+        return fail(IGA_ERR_ARG, "dt exceeds the leapfrog stability limit 2/sqrt(lambda_max)");
     cudaStream_t st = (cudaStream_t)stream;
     return w->dtype == IGA_F64 ? wave_step_typed<double>(w, nsteps, st) : wave_step_typed<float>(w, nsteps, st);
 }

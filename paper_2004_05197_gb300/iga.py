@@ -36,7 +36,7 @@ EXPORTED = [
     "iga_ops_sample_indices", "iga_stencil_apply", "iga_mass_solve", "iga_wave_create",
     "iga_wave_destroy", "iga_wave_step", "iga_wave_get_state", "iga_wave_traces",
     "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count", "iga_wave_reset",
-    "iga_wave_set_timing", "iga_wave_stats_get",
+    "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum",
 ]
 
 
@@ -73,12 +73,14 @@ class iga_wave_desc(C.Structure):
                 ("pulse_width", C.c_double), ("with_source", C.c_int),
                 ("src_pos", C.POINTER(C.c_double)), ("f0", C.c_double), ("t0", C.c_double),
                 ("src_amp", C.c_double), ("nrec", C.c_int), ("rec_pos", C.POINTER(C.c_double)),
-                ("nsteps_max", C.c_int), ("cg_rtol", C.c_double), ("cg_max_it", C.c_int)]
+                ("nsteps_max", C.c_int), ("cg_rtol", C.c_double), ("cg_max_it", C.c_int),
+                ("cfl_check", C.c_int)]
 
 
 class iga_wave_stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("cg_iterations", C.c_longlong), ("cg_solves", C.c_longlong),
-                ("cg_ms", C.c_double), ("force_ms", C.c_double)]
+                ("cg_ms", C.c_double), ("force_ms", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double)]
 
 
 _vp, _i, _u, _d = C.c_void_p, C.c_int, C.c_uint, C.c_double
@@ -103,6 +105,7 @@ _sig = {
     "iga_wave_reset": [_vp, _vp, _vp],
     "iga_wave_set_timing": [_vp, _i],
     "iga_wave_stats_get": [_vp, C.POINTER(iga_wave_stats)],
+    "iga_ops_spectrum": [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -224,7 +227,7 @@ def iga_mass_solve(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_stats=Tru
 # ---- waves ---------------------------------------------------------------------
 def iga_wave_create(ops, nshot, dtype, dt, init_kind=IGA_INIT_ZERO, pulse_centre=None, pulse_width=0.05,
                     src_pos=None, f0=10.0, t0=0.1, src_amp=1.0, rec_pos=None, nsteps_max=0,
-                    cg_rtol=1e-10, cg_max_it=1000, solve_flags=0):
+                    cg_rtol=1e-10, cg_max_it=1000, solve_flags=0, cfl_check=1):
     keep = []
 
     def hp(a):
@@ -237,7 +240,7 @@ def iga_wave_create(ops, nshot, dtype, dt, init_kind=IGA_INIT_ZERO, pulse_centre
     nrec = 0 if rec_pos is None else int(np.asarray(rec_pos).shape[0])
     desc = iga_wave_desc(nshot, dtype, solve_flags, dt, init_kind, hp(pulse_centre), pulse_width,
                          1 if src_pos is not None else 0, hp(src_pos), f0, t0, src_amp, nrec,
-                         hp(rec_pos), nsteps_max, cg_rtol, cg_max_it)
+                         hp(rec_pos), nsteps_max, cg_rtol, cg_max_it, cfl_check)
     out = C.c_void_p()
     _check(_lib.iga_wave_create(ops, C.byref(desc), C.byref(out)))
     return out
@@ -280,3 +283,10 @@ def iga_wave_stats_get(wave):
     st = iga_wave_stats()
     _check(_lib.iga_wave_stats_get(wave, C.byref(st)))
     return st
+
+
+def iga_ops_spectrum(ops, dtype=IGA_F64, k=40, stream=None):
+    """(lambda_min, lambda_max) of the pencil (K~, M~) by k Lanczos steps."""
+    lo, hi = C.c_double(), C.c_double()
+    _check(_lib.iga_ops_spectrum(ops, dtype, k, C.byref(lo), C.byref(hi), _stream(stream)))
+    return lo.value, hi.value

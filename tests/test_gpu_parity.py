@@ -318,3 +318,35 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     print(mode, "relative L2 error", err, "trace error", terr)
     tol = 1e-5 if mode == "f32" else 1e-11
     assert err <= tol and terr <= tol
+
+
+@pytest.mark.parametrize("case", ["annulus40", "cube16_M6"])
+def test_spectrum_extremes_match_dense_eigensolver(case):
+    """Lanczos (K~, M~) extremes vs scipy's dense generalized symmetric eigensolver."""
+    import scipy.linalg as sla
+    w = W.scaled("annulus512_p3", n_el=40) if case == "annulus40" else W.scaled("cube96_p2", n_el=16)
+    sp, S = oracle_surrogate(w)
+    SK, SM = S.rows(sp.all_rows())
+    lam = sla.eigh(stencil_to_csr(sp, SK).toarray(), stencil_to_csr(sp, SM).toarray(), eigvals_only=True)
+    space = W.make_space(w)
+    ops = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"])
+    lo, hi = iga.iga_ops_spectrum(ops, iga.IGA_F64, 80)
+    print(case, "lanczos", lo, hi, "dense", lam[0], lam[-1])
+    assert abs(hi - lam[-1]) <= 1e-3 * lam[-1]
+    assert abs(lo - lam[0]) <= 2e-3 * lam[-1]
+    iga.iga_ops_destroy(ops)
+
+
+def test_wave_refuses_unstable_time_step():
+    _, ops = gpu_ops("annulus64_p2")
+    lo, hi = iga.iga_ops_spectrum(ops, iga.IGA_F64, 60)
+    wave = iga.iga_wave_create(ops, 1, iga.IGA_F64, 2.5 / np.sqrt(hi), cfl_check=1)
+    with pytest.raises(iga.IgaError) as e:
+        iga.iga_wave_step(wave, 1)
+    assert e.value.code == iga.IGA_ERR_ARG
+    st = iga.iga_wave_stats_get(wave)
+    assert abs(st.lambda_max - hi) <= 1e-2 * hi
+    iga.iga_wave_destroy(wave)
+    ok = iga.iga_wave_create(ops, 1, iga.IGA_F64, 1.0 / np.sqrt(hi), cfl_check=1)
+    iga.iga_wave_step(ok, 2)
+    iga.iga_wave_destroy(ok)
