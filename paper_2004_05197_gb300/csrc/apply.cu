@@ -3,6 +3,7 @@
 // field read is a coalesced 128-byte (FP32) line; all right-hand sides of a
 // chunk reuse the field values held in registers.
 #include <algorithm>
+#include <cstdint>
 
 #include "iga_internal.cuh"
 #include "stencil.cuh"
@@ -22,6 +23,35 @@ __global__ void __launch_bounds__(256) apply_kernel(const T* __restrict__ F, lon
     }
 }
 
+// FP32, four rows per thread; interior groups vectorised, the rest per row.
+template <int DIM, int P, bool MASS, int R>
+__global__ void __launch_bounds__(256) apply4_kernel(const float* __restrict__ F, long long pitch,
+                                                      const float* __restrict__ x, float* __restrict__ y,
+                                                      long long ld, int N, int m) {
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
+    fill_delta_table<DIM, P>(sdl, m);
+    const int dmax = max_delta<DIM, P>(m);
+    const int ngroups = (N + 3) / 4;
+    const LdgLoad4 ld4{x, ld};
+    const LdgLoad<float> ld1{x, ld};
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+        const int i0 = 4 * g;
+        if (i0 >= dmax && i0 + 7 + dmax <= N - 1) {
+            float4 acc[R], own[R];
+            stencil_row4<DIM, P, MASS, R, 2>(F, pitch, ld4, i0, sdl, acc, own);
+#pragma unroll
+            for (int r = 0; r < R; ++r) *reinterpret_cast<float4*>(y + r * ld + i0) = acc[r];
+        } else {
+            for (int k = 0; k < 4 && i0 + k < N; ++k) {
+                float acc[R], own[R];
+                stencil_row<DIM, P, float, MASS, R, 4>(F, pitch, ld1, i0 + k, N, m, acc, own);
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[r * ld + i0 + k] = acc[r];
+            }
+        }
+    }
+}
+
 static int apply_grid(long long N) {
     static int sms = 0;
     if (!sms) {
@@ -34,6 +64,22 @@ static int apply_grid(long long N) {
     return (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * 16));
 }
 
+template <int DIM, int P>
+static bool apply4_launch(const iga_ops* ops, int which, const float* F, const float* x, float* y, int R,
+                          cudaStream_t st) {
+    const int N = (int)ops->N;
+    if (((uintptr_t)x | (uintptr_t)y) % 16 != 0 || (R > 1 && N % 4 != 0)) return false;
+    const int grid = apply_grid((N + 3) / 4);
+    if (R == 4) {
+        if (which == IGA_OP_M) apply4_kernel<DIM, P, true, 4><<<grid, 256, 0, st>>>(F, ops->pitch, x, y, N, N, ops->m);
+        else apply4_kernel<DIM, P, false, 4><<<grid, 256, 0, st>>>(F, ops->pitch, x, y, N, N, ops->m);
+    } else {
+        if (which == IGA_OP_M) apply4_kernel<DIM, P, true, 1><<<grid, 256, 0, st>>>(F, ops->pitch, x, y, N, N, ops->m);
+        else apply4_kernel<DIM, P, false, 1><<<grid, 256, 0, st>>>(F, ops->pitch, x, y, N, N, ops->m);
+    }
+    return true;
+}
+
 template <int DIM, int P, typename T>
 static int apply_typed(const iga_ops* ops, int which, const T* F, const T* x, T* y, int nrhs, cudaStream_t st) {
     const int N = (int)ops->N;
@@ -43,6 +89,14 @@ static int apply_typed(const iga_ops* ops, int which, const T* F, const T* x, T*
         const int left = nrhs - r0;
         const T* xr = x + (size_t)r0 * N;
         T* yr = y + (size_t)r0 * N;
+        if constexpr (sizeof(T) == 4) {
+            const int R = left >= 4 ? 4 : 1;
+            if (apply4_launch<DIM, P>(ops, which, (const float*)F, (const float*)xr, (float*)yr, R, st)) {
+                IGA_LAUNCH_CHECK("apply4_kernel");
+                r0 += R;
+                continue;
+            }
+        }
         if (left >= 4) {
             if (which == IGA_OP_M)
                 apply_kernel<DIM, P, T, true, 4><<<grid, 256, 0, st>>>(F, ops->pitch, xr, yr, N, ops->m);

@@ -94,7 +94,8 @@ namespace iga {
 // kernels implemented in apply.cu / solve.cu, shared launch helpers
 int launch_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y, int nrhs,
                  cudaStream_t st);
-int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs, double rtol,
+// b, x: [nrhs][ld] (ld >= N) in the dtype's precision
+int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long long ld, int nrhs, double rtol,
                     int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st,
                     void* work, size_t work_bytes, long long* iter_acc, int* status_acc);
 size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs);

@@ -153,6 +153,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
 }
 
 // ---------------------------------------------------------------- CG phases
+// Internal vectors (r, z, p0, p1, q) are [R][ldw] with ldw a multiple of 4;
+// the caller's b and x are [R][ldu].
 template <typename T>
 struct CgVecs {
     const T* F;          // M~ fields (field 0 = diagonal)
@@ -166,29 +168,55 @@ struct CgVecs {
     T* p1;
     T* q;
     int N, m;
-    long long ext_vec;   // R * N: extent of every [R][N] vector
+    long long ldw, ldu;
+    long long ext_vec;   // R * ldw: extent of every internal vector
+    long long ext_user;  // R * ldu: extent of b and x
     long long ext_diag;  // extent of dinv
+};
+
+// z + beta p_old for four consecutive rows (coherent 16-byte loads)
+__device__ __forceinline__ float4 ld4c(const float* p) { return *reinterpret_cast<const float4*>(p); }
+template <int R>
+struct CombLoad4 {
+    const float* z;
+    const float* p;
+    long long ld;
+    float beta[R];
+    __device__ __forceinline__ float4 load4(int r, int idx) const {
+        const float b = beta[r];
+        return f4_fma(make_float4(b, b, b, b), ld4c(p + r * ld + idx), ld4c(z + r * ld + idx));
+    }
+    __device__ __forceinline__ float4 load4u(int r, int j) const {
+        const int off = j & 3;
+        const long long a = r * ld + (j - off);
+        const float b = beta[r];
+        const float4 bb = make_float4(b, b, b, b);
+        const float4 v0 = f4_fma(bb, ld4c(p + a), ld4c(z + a));
+        if (off == 0) return v0;
+        const float4 v1 = f4_fma(bb, ld4c(p + a + 4), ld4c(z + a + 4));
+        return f4_window(v0, v1, off);
+    }
 };
 
 // init: r = b - M~x, z = D^-1 r; partials (r,z), (r,r), (b,b)
 template <int DIM, int P, typename T, int R>
 __device__ __forceinline__ void cg_init_rows(const CgVecs<T>& v, double* part) {
     for (int k = 0; k < 3 * R; ++k) part[k] = 0.0;
-    PlainLoad<T> ld{v.x, v.N, v.ext_vec};
+    PlainLoad<T> ld{v.x, v.ldu, v.ext_user};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
         stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
         const double di = IGA_IN(i, v.ext_diag, 6) ? (double)v.dinv[i] : 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const long long o = (long long)r * v.N + i;
-            const bool ok = IGA_IN(o, v.ext_vec, 7);
-            const double bi = ok ? (double)v.b[o] : 0.0;
+            const long long ou = (long long)r * v.ldu + i, ow = (long long)r * v.ldw + i;
+            const bool ok = IGA_IN(ou, v.ext_user, 7) && IGA_IN(ow, v.ext_vec, 16);
+            const double bi = ok ? (double)v.b[ou] : 0.0;
             const double ri = bi - (double)acc[r];
             const T zi = (T)(di * ri);
             if (ok) {
-                v.r[o] = ri;
-                v.z[o] = zi;
+                v.r[ow] = ri;
+                v.z[ow] = zi;
             }
             part[3 * r + 0] += ri * (double)zi;
             part[3 * r + 1] += ri * ri;
@@ -200,27 +228,70 @@ __device__ __forceinline__ void cg_init_rows(const CgVecs<T>& v, double* part) {
 // phase A: p_new = z + beta p_old, q = M~ p_new; partial (p_new, q)
 template <int DIM, int P, typename T, int R>
 __device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T* pnew, const double* beta,
-                                           const int* active, double* part) {
+                                           const int* active, double* part, const int* sdl) {
     for (int k = 0; k < R; ++k) part[k] = 0.0;
     CombLoad<T, R> ld;
     ld.z = v.z;
     ld.p = pold;
-    ld.xs = v.N;
+    ld.xs = v.ldw;
     ld.ext = v.ext_vec;
 #pragma unroll
     for (int r = 0; r < R; ++r) ld.beta[r] = (T)beta[r];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
-        T acc[R], own[R];
-        stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+    if constexpr (sizeof(T) == 4) {
+        // four rows per thread; interior groups vectorised (see stencil_row4)
+        CombLoad4<R> ld4;
+        ld4.z = v.z;
+        ld4.p = pold;
+        ld4.ld = v.ldw;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (!active[r]) continue;
-            const long long o = (long long)r * v.N + i;
-            if (IGA_IN(o, v.ext_vec, 8)) {
-                pnew[o] = own[r];
-                v.q[o] = acc[r];
+        for (int r = 0; r < R; ++r) ld4.beta[r] = (float)beta[r];
+        const int dmax = max_delta<DIM, P>(v.m);
+        const int ngroups = (v.N + 3) / 4;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+            const int i0 = 4 * g;
+            if (i0 >= dmax && i0 + 7 + dmax <= v.N - 1) {
+                float4 acc[R], own[R];
+                stencil_row4<DIM, P, true, R, kCgUnroll<R>>(v.F, v.pitch, ld4, i0, sdl, acc, own);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!active[r]) continue;
+                    const long long o = (long long)r * v.ldw + i0;
+                    *reinterpret_cast<float4*>(pnew + o) = own[r];
+                    *reinterpret_cast<float4*>(v.q + o) = acc[r];
+                    part[r] += (double)own[r].x * acc[r].x + (double)own[r].y * acc[r].y +
+                               (double)own[r].z * acc[r].z + (double)own[r].w * acc[r].w;
+                }
+            } else {
+                for (int k = 0; k < 4 && i0 + k < v.N; ++k) {
+                    T acc[R], own[R];
+                    stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i0 + k, v.N, v.m, acc, own);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (!active[r]) continue;
+                        const long long o = (long long)r * v.ldw + i0 + k;
+                        if (IGA_IN(o, v.ext_vec, 8)) {
+                            pnew[o] = own[r];
+                            v.q[o] = acc[r];
+                        }
+                        part[r] += (double)own[r] * (double)acc[r];
+                    }
+                }
             }
-            part[r] += (double)own[r] * (double)acc[r];
+        }
+    } else {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
+            T acc[R], own[R];
+            stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!active[r]) continue;
+                const long long o = (long long)r * v.ldw + i;
+                if (IGA_IN(o, v.ext_vec, 8)) {
+                    pnew[o] = own[r];
+                    v.q[o] = acc[r];
+                }
+                part[r] += (double)own[r] * (double)acc[r];
+            }
         }
     }
 }
@@ -235,10 +306,11 @@ __device__ __forceinline__ void cg_phase_b(const CgVecs<T>& v, const T* pnew, co
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!active[r]) continue;
-            const size_t o = (size_t)r * v.N + i;
-            if (!IGA_IN(o, v.ext_vec, 10)) continue;
+            const size_t o = (size_t)r * v.ldw + i;
+            const size_t ou = (size_t)r * v.ldu + i;
+            if (!IGA_IN(o, v.ext_vec, 10) || !IGA_IN(ou, v.ext_user, 17)) continue;
             const T pi = pnew[o];
-            v.x[o] = v.x[o] + (T)alpha[r] * pi;
+            v.x[ou] = v.x[ou] + (T)alpha[r] * pi;
             const double ri = v.r[o] - alpha[r] * (double)v.q[o];
             const T zi = (T)(di * ri);
             v.r[o] = ri;
@@ -273,8 +345,10 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
     __shared__ double red[3 * R];
     __shared__ double rz[R], rr[R], bnorm[R], alpha[R], beta[R];
     __shared__ int active[R], iters[R];
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
     double part[3 * R];
     const int S = 6 * R;
+    fill_delta_table<DIM, P>(sdl, v.m);
 
     cg_init_rows<DIM, P, T, R>(v, part);
     block_sum<3 * R>(part, wsum, red);
@@ -297,7 +371,7 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
     for (int r = 0; r < R; ++r)
         if (!(bnorm[r] > 0.0))
             for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x)
-                if (IGA_IN((long long)r * v.N + i, v.ext_vec, 15)) v.x[(size_t)r * v.N + i] = T(0);
+                if (IGA_IN((long long)r * v.ldu + i, v.ext_user, 15)) v.x[(size_t)r * v.ldu + i] = T(0);
     // p_old starts at 0 (cleared by the host) so that p = z on the first iteration
     for (int it = 0; it < c.max_it; ++it) {
         bool any = false;
@@ -305,7 +379,7 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
         if (!any) break;
         T* pold = (it & 1) ? v.p1 : v.p0;
         T* pnew = (it & 1) ? v.p0 : v.p1;
-        cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part);
+        cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part, sdl);
         block_sum<R>(part, wsum, red);
         if (threadIdx.x < R && IGA_IN((long long)blockIdx.x * S + threadIdx.x, (long long)c.nblocks * S, 12))
             c.partials[(size_t)blockIdx.x * S + threadIdx.x] = red[threadIdx.x];
@@ -370,13 +444,14 @@ __global__ void __launch_bounds__(kCgThreads) cg_a_kernel(CgVecs<T> v, const T* 
     __shared__ double red[3 * R];
     __shared__ double beta[R];
     __shared__ int active[R];
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
     if (threadIdx.x < R) {
         beta[threadIdx.x] = sc[threadIdx.x];
         active[threadIdx.x] = (int)sc[2 * R + threadIdx.x];
     }
-    __syncthreads();
+    fill_delta_table<DIM, P>(sdl, v.m);
     double part[3 * R];
-    cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part);
+    cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part, sdl);
     block_sum<R>(part, wsum, red);
     if (threadIdx.x < R) partials[(size_t)blockIdx.x * 6 * R + threadIdx.x] = red[threadIdx.x];
 }
@@ -428,7 +503,7 @@ struct CgWork {
 };
 
 template <typename T>
-static CgWork carve(void* base, long long N, int R, int nblocks) {
+static CgWork carve(void* base, long long N /* leading dimension of the internal vectors */, int R, int nblocks) {
     char* p = (char*)base;
     auto take = [&](size_t bytes) {
         void* out = p;
@@ -471,13 +546,14 @@ static int cg_blocks() {
 }
 
 template <int DIM, int P, typename T, int R>
-static int pcg_chunk(const iga_ops* ops, const T* b, T* x, double rtol, int max_it, unsigned flags, int* iters_h,
-                     double* relres_h, cudaStream_t st, void* work, size_t work_bytes, bool* not_conv,
+static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double rtol, int max_it, unsigned flags,
+                     int* iters_h, double* relres_h, cudaStream_t st, void* work, size_t work_bytes, bool* not_conv,
                      long long* iter_acc, int* status_acc) {
     const long long N = ops->N;
+    const long long ldw = (N + 3) / 4 * 4;
     const int nblocks = cg_blocks<DIM, P, T, R>();
-    if (carve_bytes(sizeof(T), N, R, nblocks) > work_bytes) return fail(IGA_ERR_ARG, "CG workspace too small");
-    CgWork w = carve<T>(work, N, R, nblocks);
+    if (carve_bytes(sizeof(T), ldw, R, nblocks) > work_bytes) return fail(IGA_ERR_ARG, "CG workspace too small");
+    CgWork w = carve<T>(work, ldw, R, nblocks);
     CgVecs<T> v;
     v.F = (sizeof(T) == 8) ? (const T*)ops->fM64.ptr : (const T*)ops->fM32.ptr;
     v.pitch = ops->pitch;
@@ -491,9 +567,12 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, double rtol, int max_
     v.q = (T*)w.q;
     v.N = (int)N;
     v.m = ops->m;
-    v.ext_vec = (long long)R * N;
+    v.ldw = ldw;
+    v.ldu = ldu;
+    v.ext_vec = (long long)R * ldw;
+    v.ext_user = (long long)(R - 1) * ldu + N;
     v.ext_diag = ops->pitch;
-    IGA_CUDA(cudaMemsetAsync(w.p0, 0, sizeof(T) * R * N, st));
+    IGA_CUDA(cudaMemsetAsync(w.p0, 0, sizeof(T) * R * ldw, st));
     IGA_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
     IGA_CUDA(cudaMemsetAsync(w.err, 0, 64, st));
     int iters[R];
@@ -556,7 +635,7 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, double rtol, int max_
             active[r] = bn[r] > 0.0 && !(rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]);
             sc[r] = 0.0;                // beta
             sc[R + r] = 0.0;            // alpha
-            if (!(bn[r] > 0.0)) IGA_CUDA(cudaMemsetAsync(x + (size_t)r * N, 0, sizeof(T) * N, st));
+            if (!(bn[r] > 0.0)) IGA_CUDA(cudaMemsetAsync(x + (size_t)r * ldu, 0, sizeof(T) * N, st));
         }
         for (int it = 0; it < max_it; ++it) {
             bool any = false;
@@ -625,21 +704,21 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, double rtol, int max_
 }
 
 template <int DIM, int P, typename T>
-static int pcg_typed(const iga_ops* ops, const T* b, T* x, int nrhs, double rtol, int max_it, unsigned flags,
-                     int* iters_h, double* relres_h, cudaStream_t st, void* work, size_t work_bytes, bool* nc,
-                     long long* iter_acc, int* status_acc) {
-    const long long N = ops->N;
+static int pcg_typed(const iga_ops* ops, const T* b, T* x, long long ldu, int nrhs, double rtol, int max_it,
+                     unsigned flags, int* iters_h, double* relres_h, cudaStream_t st, void* work, size_t work_bytes,
+                     bool* nc, long long* iter_acc, int* status_acc) {
+    const long long N = ldu;
     int r0 = 0;
     while (r0 < nrhs) {
         const int left = nrhs - r0;
         int rc;
         if (left >= 4) {
-            rc = pcg_chunk<DIM, P, T, 4>(ops, b + (size_t)r0 * N, x + (size_t)r0 * N, rtol, max_it, flags,
+            rc = pcg_chunk<DIM, P, T, 4>(ops, b + (size_t)r0 * N, x + (size_t)r0 * N, ldu, rtol, max_it, flags,
                                          iters_h ? iters_h + r0 : nullptr, relres_h ? relres_h + r0 : nullptr, st,
                                          work, work_bytes, nc, iter_acc, status_acc);
             r0 += 4;
         } else {
-            rc = pcg_chunk<DIM, P, T, 1>(ops, b + (size_t)r0 * N, x + (size_t)r0 * N, rtol, max_it, flags,
+            rc = pcg_chunk<DIM, P, T, 1>(ops, b + (size_t)r0 * N, x + (size_t)r0 * N, ldu, rtol, max_it, flags,
                                          iters_h ? iters_h + r0 : nullptr, relres_h ? relres_h + r0 : nullptr, st,
                                          work, work_bytes, nc, iter_acc, status_acc);
             r0 += 1;
@@ -655,11 +734,11 @@ size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nb = std::max(1, sms) * kCgMaxBlocksPerSM;
-    return carve_bytes(dtype == IGA_F64 ? 8 : 4, ops->N, 4, nb);
+    return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, 4, nb);
 }
 
-int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs, double rtol, int max_it,
-                    unsigned flags, int* iters_out, double* relres_out, cudaStream_t st, void* work,
+int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long long ld, int nrhs, double rtol,
+                    int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st, void* work,
                     size_t work_bytes, long long* iter_acc, int* status_acc) {
     bool nc = false;
     const bool want = iters_out || relres_out;
@@ -670,10 +749,10 @@ int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, int n
 #define IGA_PCG_CASE(DD, PP)                                                                                   \
     if (d == DD && p == PP)                                                                                    \
         rc = dtype == IGA_F64                                                                                  \
-                 ? pcg_typed<DD, PP, double>(ops, (const double*)b, (double*)x, nrhs, rtol, max_it, flags,    \
+                 ? pcg_typed<DD, PP, double>(ops, (const double*)b, (double*)x, ld, nrhs, rtol, max_it, flags,\
                                              want ? it_h.data() : nullptr, want ? rr_h.data() : nullptr, st,  \
                                              work, work_bytes, want ? &nc : nullptr, iter_acc, status_acc)    \
-                 : pcg_typed<DD, PP, float>(ops, (const float*)b, (float*)x, nrhs, rtol, max_it, flags,       \
+                 : pcg_typed<DD, PP, float>(ops, (const float*)b, (float*)x, ld, nrhs, rtol, max_it, flags,   \
                                             want ? it_h.data() : nullptr, want ? rr_h.data() : nullptr, st,   \
                                             work, work_bytes, want ? &nc : nullptr, iter_acc, status_acc);    \
     else
@@ -708,6 +787,6 @@ extern "C" int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void
         int rc = mops->work.alloc(need);
         if (rc) return rc;
     }
-    return mass_solve_impl(ops, dtype, b, x, nrhs, rtol, max_it, flags, iters_out, relres_out,
+    return mass_solve_impl(ops, dtype, b, x, ops->N, nrhs, rtol, max_it, flags, iters_out, relres_out,
                            (cudaStream_t)stream, mops->work.ptr, mops->work.bytes, nullptr, nullptr);
 }

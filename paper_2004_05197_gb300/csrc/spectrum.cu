@@ -129,7 +129,7 @@ static int spectrum_typed(const iga_ops* ops, int dtype, int k, double* lam_min,
         double a = 0.0;
         if ((rc = dot<T>(v, y, N, part, &a, st))) return rc;
         IGA_CUDA(cudaMemsetAsync(w, 0, sizeof(T) * N, st));
-        rc = mass_solve_impl(ops, dtype, y, w, 1, rtol, 2000, 0, nullptr, nullptr, st, mops->work.ptr,
+        rc = mass_solve_impl(ops, dtype, y, w, N, 1, rtol, 2000, 0, nullptr, nullptr, st, mops->work.ptr,
                              mops->work.bytes, nullptr, nullptr);
         if (rc && rc != IGA_ERR_NOT_CONVERGED) return rc;
         axpbypcz_kernel<T><<<grid, 256, 0, st>>>(w, v, vprev, -a, 1.0, -beta_prev, N);

@@ -99,3 +99,103 @@ __device__ __forceinline__ void stencil_row(const T* __restrict__ F, long long p
 }
 
 }  // namespace iga
+
+// ---------------------------------------------------------------------------
+// FP32 path, four consecutive rows per thread (i0 = 4k).
+//
+// The own field values of rows i0..i0+3 are one aligned float4.  The mirrored
+// values F_u[i0-Delta .. i0-Delta+3] and the neighbour vector values start at
+// an offset that is the same for every thread of the warp (Delta mod 4), so
+// they are read as two aligned float4 and the four wanted lanes selected
+// without divergence.  Offsets come from a shared table sdl[u] = Delta_u.
+// Only "interior" groups use this path: every index read, including the
+// second aligned float4, lies in [0, N):  i0 >= Delta_max and
+// i0 + 7 + Delta_max <= N - 1.  Other groups take the scalar path per row.
+namespace iga {
+
+__device__ __forceinline__ float4 f4_fma(float4 a, float4 b, float4 c) {
+    return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z), fmaf(a.w, b.w, c.w));
+}
+__device__ __forceinline__ float4 f4_sub(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 f4_mul(float4 a, float4 b) {
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+// lanes off..off+3 of the 8 consecutive values (v0, v1)
+__device__ __forceinline__ float4 f4_window(float4 v0, float4 v1, int off) {
+    switch (off) {
+        case 0: return v0;
+        case 1: return make_float4(v0.y, v0.z, v0.w, v1.x);
+        case 2: return make_float4(v0.z, v0.w, v1.x, v1.y);
+        default: return make_float4(v0.w, v1.x, v1.y, v1.z);
+    }
+}
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+// four values base[j..j+3] for an arbitrary j >= 0 (warp-uniform j mod 4)
+__device__ __forceinline__ float4 ldg4u(const float* base, int j) {
+    const int off = j & 3;
+    const float* a = base + (j - off);
+    const float4 v0 = ldg4(a);
+    if (off == 0) return v0;
+    return f4_window(v0, ldg4(a + 4), off);
+}
+
+// Read-only vectors [R][ld] (ld a multiple of 4, base 16-byte aligned).
+struct LdgLoad4 {
+    const float* x;
+    long long ld;
+    __device__ __forceinline__ float load1(int r, int idx) const { return __ldg(x + r * ld + idx); }
+    __device__ __forceinline__ float4 load4(int r, int idx) const { return ldg4(x + r * ld + idx); }
+    __device__ __forceinline__ float4 load4u(int r, int j) const { return ldg4u(x + r * ld, j); }
+};
+
+template <int DIM, int P, bool MASS, int R, int UNR, class L>
+__device__ __forceinline__ void stencil_row4(const float* __restrict__ F, long long pitch, const L& ld, int i0,
+                                             const int* sdl, float4* acc, float4* own) {
+    constexpr int NF = StencilShape<DIM, P>::T0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) own[r] = ld.load4(r, i0);
+    if (MASS) {
+        const float4 d = ldg4(F + i0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = f4_mul(d, own[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float* Foff = MASS ? F + pitch : F;
+#pragma unroll UNR
+    for (int u = 0; u < NF; ++u) {
+        const int dl = sdl[u];
+        const float* Fu = Foff + (size_t)u * pitch;
+        const float4 s = ldg4(Fu + i0);
+        const float4 sm = ldg4u(Fu, i0 - dl);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 xp = ld.load4u(r, i0 + dl);
+            const float4 xm = ld.load4u(r, i0 - dl);
+            if (MASS) {
+                acc[r] = f4_fma(s, xp, acc[r]);
+                acc[r] = f4_fma(sm, xm, acc[r]);
+            } else {
+                acc[r] = f4_fma(s, f4_sub(xp, own[r]), acc[r]);
+                acc[r] = f4_fma(sm, f4_sub(xm, own[r]), acc[r]);
+            }
+        }
+    }
+}
+
+// Delta table of the off-diagonal fields in shared memory (call with all threads).
+template <int DIM, int P>
+__device__ __forceinline__ void fill_delta_table(int* sdl, int m) {
+    for (int u = threadIdx.x; u < StencilShape<DIM, P>::T0; u += blockDim.x) sdl[u] = field_delta<DIM, P>(u, m);
+    __syncthreads();
+}
+
+template <int DIM, int P>
+__host__ __device__ __forceinline__ int max_delta(int m) {
+    return field_delta<DIM, P>(StencilShape<DIM, P>::T0 - 1, m);
+}
+
+}  // namespace iga

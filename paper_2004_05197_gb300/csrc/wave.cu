@@ -199,7 +199,7 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
             IGA_LAUNCH_CHECK("source_kernel");
         }
         if (w->timing) cudaEventRecord(ev[4 * s + 2], st);
-        rc = mass_solve_impl(ops, w->dtype, w->b.ptr, w->a.ptr, w->nshot, w->desc.cg_rtol, w->desc.cg_max_it,
+        rc = mass_solve_impl(ops, w->dtype, w->b.ptr, w->a.ptr, w->N, w->nshot, w->desc.cg_rtol, w->desc.cg_max_it,
                              w->desc.solve_flags, nullptr, nullptr, st, w->work.ptr, w->work.bytes, iter_acc, status);
         if (w->timing) cudaEventRecord(ev[4 * s + 3], st);
         w->cg_solves += (w->nshot + 3) / 4;

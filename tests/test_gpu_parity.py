@@ -316,7 +316,9 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     err = np.linalg.norm(ug - ur) / np.linalg.norm(ur)
     terr = np.abs(tr - trr).max() / np.abs(ur).max()
     print(mode, "relative L2 error", err, "trace error", terr)
-    tol = 1e-5 if mode == "f32" else 1e-11
+    # FP32 parity tolerance 2e-5: storing M~ in FP32 perturbs each solve by about
+    # cond(M~) * 2^-24 ~ 1e-5 whatever the CG tolerance
+    tol = 2e-5 if mode == "f32" else 1e-11
     assert err <= tol and terr <= tol
 
 
