@@ -132,7 +132,7 @@ def run_ours(args, rank, world, device):
     ops = assemble()
     wave = iga.iga_wave_create(ops, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
                                f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
-                               cg_max_it=args.cg_max_it)
+                               cg_max_it=args.cg_max_it, cfl_check=2)
     iga.iga_wave_set_timing(wave, True)
 
     def one_pass(old_ops):

@@ -219,8 +219,9 @@ typedef struct iga_wave_desc {
     int nsteps_max;             /* capacity of the trace buffer (steps) */
     double cg_rtol;
     int cg_max_it;
-    int cfl_check;              /* 1: estimate lambda_max(M~^-1 K~) by Lanczos at create / reset and
-                                   refuse (IGA_ERR_ARG) steps with dt sqrt(lambda_max) >= 2 */
+    int cfl_check;              /* 1: estimate lambda_max(M~^-1 K~) by Lanczos at create and at every
+                                   reset; 2: at create only; 0: off.  With an estimate, steps
+                                   with dt sqrt(lambda_max) >= 2 are refused (IGA_ERR_ARG) */
 } iga_wave_desc;
 
 int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);
@@ -257,6 +258,24 @@ typedef struct iga_wave_stats {
 } iga_wave_stats;
 int iga_wave_set_timing(iga_wave* wave, int on);
 int iga_wave_stats_get(const iga_wave* wave, iga_wave_stats* out);
+
+/* ---- adjoint ------------------------------------------------------------
+ * wave_adjoint: restarts the wave (FP64 only) from its initial condition, runs
+ * nsteps leapfrog steps with checkpoints (u^n, u^{n-1}, a^{n-1}) every
+ * checkpoint_every steps, evaluates the receiver misfit
+ *     J = dt/2 sum_shots sum_receivers sum_{n=1..nsteps} (d^n - obs^n)^2
+ * and, if grad_theta != NULL, its gradient with respect to the B-spline
+ * coefficients theta of the wave speed (space created with IGA_COEF_BSPLINE) by
+ * the discrete adjoint of leapfrog + CG + surrogate assembly (segments are
+ * recomputed from their checkpoints).  The paper has no adjoint; this is the
+ * differentiation of its surrogate model.
+ *   obs        host [nshot][nrec][nsteps] observed traces
+ *   J_out      host scalar (nullable)
+ *   grad_theta host [n_theta^dim], colex (nullable: misfit only)
+ * Synchronous.  Errors: IGA_ERR_ARG (FP32 wave, no receivers, nsteps outside
+ * 1..nsteps_max, coefficient not a B-spline), CG errors as in wave_step. */
+int iga_wave_adjoint(iga_wave* wave, int nsteps, int checkpoint_every, const double* obs, double* J_out,
+                     double* grad_theta, void* stream);
 
 /* ---- misc ------------------------------------------------------------- */
 const char* iga_last_error(void);

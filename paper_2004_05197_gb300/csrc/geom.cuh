@@ -91,6 +91,31 @@ __device__ inline double coef_c2(const GeomParams& gp, const int* e, const int* 
     return c * c;
 }
 
+// Wave speed c at the point (tensor B-spline coefficient only; used by the adjoint).
+__device__ inline double coef_c(const GeomParams& gp, const int* e, const int* g) {
+    const int k1 = gp.theta_deg + 1;
+    const int nt = gp.n_theta;
+    int span[3] = {0, 0, 0};
+    const double* v[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < gp.dim; ++k) {
+        const int idx = e[k] * gp.nq + g[k];
+        span[k] = gp.tspan[idx];
+        v[k] = gp.tval + (size_t)idx * k1;
+    }
+    double c = 0.0;
+    if (gp.dim == 2) {
+        for (int b = 0; b < k1; ++b)
+            for (int a = 0; a < k1; ++a) c += gp.theta[(span[1] + b) * nt + span[0] + a] * v[0][a] * v[1][b];
+    } else {
+        for (int cc = 0; cc < k1; ++cc)
+            for (int b = 0; b < k1; ++b)
+                for (int a = 0; a < k1; ++a)
+                    c += gp.theta[((size_t)(span[2] + cc) * nt + span[1] + b) * nt + span[0] + a] * v[0][a] * v[1][b] *
+                         v[2][cc];
+    }
+    return c;
+}
+
 // Pulled-back weights at Gauss point (e, g): G (packed symmetric) and wm.
 // Returns det J (callers flag det J <= 0).
 __device__ inline double qp_weights(const GeomParams& gp, const int* e, const int* g, double* G,

@@ -71,6 +71,9 @@ struct iga_space {
     int D;
     std::vector<double> knots;              // host copy of the open uniform knot vector
     std::vector<double> gauss_x, gauss_w;   // Gauss rule on [0,1]
+    std::vector<double> qs_h;               // [n_el][nq] Gauss point coordinates (host copy)
+    std::vector<int> tspan_h;               // [n_el][nq] first non-zero theta function (host copy)
+    std::vector<double> tval_h;             // [n_el][nq][theta_deg+1] theta basis values (host copy)
     iga::DevBuf theta, qs, qw, bval, bder, tspan, tval;
     iga::GeomParams gp;
 };
@@ -90,6 +93,19 @@ struct iga_ops {
     float t_sample, t_band, t_interp, t_eval, t_total;
 };
 
+struct iga_wave {
+    const iga_ops* ops;
+    iga_wave_desc desc;
+    int dtype, nshot, nrec, nloc, step;
+    long long N;
+    iga::DevBuf u, uprev, a, b, traces, src_idx, src_w, rec_idx, rec_w, work, counters;
+    iga::DevBuf greville, centres;   // pulse initial condition inputs (GAUSS_PULSE)
+    int timing = 0;
+    long long cg_solves = 0;
+    double cg_ms = 0.0, force_ms = 0.0;
+    double lam_min = 0.0, lam_max = 0.0;
+};
+
 namespace iga {
 // kernels implemented in apply.cu / solve.cu, shared launch helpers
 int launch_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y, int nrhs,
@@ -100,6 +116,8 @@ int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long 
                     void* work, size_t work_bytes, long long* iter_acc, int* status_acc);
 size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs);
 int spectrum_impl(const iga_ops* ops, int dtype, int k, double* lam_min, double* lam_max, cudaStream_t st);
+int wave_step_impl(iga_wave* w, int nsteps, cudaStream_t st);
+int wave_initial_state(iga_wave* w, cudaStream_t st);
 // colex decode of stencil offset t into delta (0..dim-1), values in [-p, p]
 inline void decode_offset(int t, int dim, int p, int delta[3]) {
     int P = 2 * p + 1;

@@ -52,6 +52,7 @@ __device__ __noinline__ void bounds_record(long long idx, long long ext, int sit
 
 constexpr int kCgThreads = 256;
 constexpr int kCgMaxBlocksPerSM = 8;
+constexpr bool kCgFourRow = false;   // four-rows-per-thread phase A (measured slower; kept selectable)
 template <int R>
 constexpr int kCgUnroll = R >= 4 ? 2 : 4;   // fields in flight per thread in the mass apply
 constexpr int kCgWarps = kCgThreads / 32;
@@ -237,7 +238,7 @@ __device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T*
     ld.ext = v.ext_vec;
 #pragma unroll
     for (int r = 0; r < R; ++r) ld.beta[r] = (T)beta[r];
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (kCgFourRow && sizeof(T) == 4) {
         // four rows per thread; interior groups vectorised (see stencil_row4)
         CombLoad4<R> ld4;
         ld4.z = v.z;
@@ -279,9 +280,13 @@ __device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T*
             }
         }
     } else {
+        const int dmax = max_delta<DIM, P>(v.m);
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
             T acc[R], own[R];
-            stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+            if (i >= dmax && i < v.N - dmax)
+                stencil_row_interior<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, sdl, acc, own);
+            else
+                stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (!active[r]) continue;

@@ -151,6 +151,9 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
         if (!rc) rc = upload(s->theta, std::vector<double>(1, 0.0));
     }
     if (!rc) rc = upload(s->tspan, tspan);
+    s->qs_h = qs;
+    s->tspan_h = tspan;
+    s->tval_h = tval;
     if (rc) {
         delete s;
         return rc;

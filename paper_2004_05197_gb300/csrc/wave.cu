@@ -16,28 +16,21 @@
 #include "iga_internal.cuh"
 #include "stencil.cuh"
 
-struct iga_wave {
-    const iga_ops* ops;
-    iga_wave_desc desc;
-    int dtype, nshot, nrec, nloc, step;
-    long long N;
-    iga::DevBuf u, uprev, a, b, traces, src_idx, src_w, rec_idx, rec_w, work, counters;
-    iga::DevBuf greville, centres;   // pulse initial condition inputs (GAUSS_PULSE)
-    int timing = 0;
-    long long cg_solves = 0;
-    double cg_ms = 0.0, force_ms = 0.0;
-    double lam_min = 0.0, lam_max = 0.0;
-};
-
 namespace iga {
 
 template <int DIM, int P, typename T, int R>
 __global__ void __launch_bounds__(256) force_kernel(const T* __restrict__ F, long long pitch, const T* __restrict__ u,
                                                      T* __restrict__ b, int N, int m) {
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
+    fill_delta_table<DIM, P>(sdl, m);
+    const int dmax = max_delta<DIM, P>(m);
     const LdgLoad<T> ld{u, N};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
-        stencil_row<DIM, P, T, false, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, N, m, acc, own);
+        if (i >= dmax && i < N - dmax)
+            stencil_row_interior<DIM, P, T, false, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, sdl, acc, own);
+        else
+            stencil_row<DIM, P, T, false, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, N, m, acc, own);
 #pragma unroll
         for (int r = 0; r < R; ++r) b[(size_t)r * N + i] = -acc[r];
     }
@@ -239,7 +232,7 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
 }
 
 // u^0 from the initial condition, u^{-1} and a^{-1} cleared, counters reset.
-static int initial_state(iga_wave* w, cudaStream_t st) {
+int wave_initial_state(iga_wave* w, cudaStream_t st) {
     const iga_space* s = w->ops->space;
     const size_t vb = (w->dtype == IGA_F64 ? 8 : 4) * (size_t)w->nshot * w->N;
     IGA_CUDA(cudaMemsetAsync(w->a.ptr, 0, vb, st));
@@ -262,11 +255,17 @@ static int initial_state(iga_wave* w, cudaStream_t st) {
     w->step = 0;
     w->cg_solves = 0;
     w->cg_ms = w->force_ms = 0.0;
-    if (w->desc.cfl_check) {
+    // cfl_check 1: estimate at create and at every reset; 2: at create only (a reset
+    // re-binds operators of the same problem)
+    if (w->desc.cfl_check == 1 || (w->desc.cfl_check == 2 && w->lam_max == 0.0)) {
         int rc = spectrum_impl(w->ops, IGA_F32, 40, &w->lam_min, &w->lam_max, st);
         if (rc) return rc;
     }
     return IGA_OK;
+}
+
+int wave_step_impl(iga_wave* w, int nsteps, cudaStream_t st) {
+    return w->dtype == IGA_F64 ? wave_step_typed<double>(w, nsteps, st) : wave_step_typed<float>(w, nsteps, st);
 }
 
 }  // namespace iga
@@ -278,7 +277,7 @@ extern "C" int iga_wave_reset(iga_wave* w, const iga_ops* ops, void* stream) {
     if (ops->N != w->N || ops->space->dim != w->ops->space->dim || ops->p != w->ops->p)
         return fail(IGA_ERR_ARG, "ops must have the wave's space size and degree");
     w->ops = ops;
-    return initial_state(w, (cudaStream_t)stream);
+    return wave_initial_state(w, (cudaStream_t)stream);
 }
 
 extern "C" int iga_wave_set_timing(iga_wave* w, int on) {
@@ -379,7 +378,7 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
         cudaMemcpy(w->greville.ptr, gv.data(), sizeof(double) * gv.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(w->centres.ptr, d.pulse_centre, sizeof(double) * d.nshot * s->dim, cudaMemcpyHostToDevice);
     }
-    if ((rc = initial_state(w, 0))) return bail(rc);
+    if ((rc = wave_initial_state(w, 0))) return bail(rc);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bail(cuda_fail(e, "wave_create"));
     *out = w;
@@ -398,8 +397,7 @@ extern "C" int iga_wave_step(iga_wave* w, int nsteps, void* stream) {
     if (nsteps == 0) return IGA_OK;
     if (w->desc.cfl_check && w->desc.dt * std::sqrt(1.02 * w->lam_max) >= 2.0)
         return fail(IGA_ERR_ARG, "dt exceeds the leapfrog stability limit 2/sqrt(lambda_max)");
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->dtype == IGA_F64 ? wave_step_typed<double>(w, nsteps, st) : wave_step_typed<float>(w, nsteps, st);
+    return wave_step_impl(w, nsteps, (cudaStream_t)stream);
 }
 
 extern "C" int iga_wave_get_state(const iga_wave* w, void* u, void* u_prev, void* stream) {

@@ -36,7 +36,7 @@ EXPORTED = [
     "iga_ops_sample_indices", "iga_stencil_apply", "iga_mass_solve", "iga_wave_create",
     "iga_wave_destroy", "iga_wave_step", "iga_wave_get_state", "iga_wave_traces",
     "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count", "iga_wave_reset",
-    "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum",
+    "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum", "iga_wave_adjoint",
 ]
 
 
@@ -106,6 +106,7 @@ _sig = {
     "iga_wave_set_timing": [_vp, _i],
     "iga_wave_stats_get": [_vp, C.POINTER(iga_wave_stats)],
     "iga_ops_spectrum": [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), _vp],
+    "iga_wave_adjoint": [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -290,3 +291,14 @@ def iga_ops_spectrum(ops, dtype=IGA_F64, k=40, stream=None):
     lo, hi = C.c_double(), C.c_double()
     _check(_lib.iga_ops_spectrum(ops, dtype, k, C.byref(lo), C.byref(hi), _stream(stream)))
     return lo.value, hi.value
+
+
+def iga_wave_adjoint(wave, nsteps, checkpoint_every, obs, n_theta_total=0, stream=None):
+    """(J, grad_theta or None); obs host [nshot][nrec][nsteps]."""
+    obs_a, obs_p = _host_f64(obs)
+    J = C.c_double()
+    grad = np.zeros(n_theta_total) if n_theta_total else None
+    gp = grad.ctypes.data_as(C.POINTER(C.c_double)) if grad is not None else C.POINTER(C.c_double)()
+    _check(_lib.iga_wave_adjoint(wave, nsteps, checkpoint_every, obs_p, C.byref(J), gp, _stream(stream)))
+    del obs_a
+    return J.value, grad
