@@ -50,9 +50,8 @@ __device__ __noinline__ void bounds_record(long long idx, long long ext, int sit
 #define IGA_IN(idx, ext, site) true
 #endif
 
-constexpr int kCgThreads = 256;
-constexpr int kCgMaxBlocksPerSM = 8;
-constexpr bool kCgFourRow = false;   // four-rows-per-thread phase A (measured slower; kept selectable)
+constexpr int kCgThreads = 768;
+constexpr int kCgMaxBlocksPerSM = 2;
 template <int R>
 constexpr int kCgUnroll = R >= 4 ? 2 : 4;   // fields in flight per thread in the mass apply
 constexpr int kCgWarps = kCgThreads / 32;
@@ -154,8 +153,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
 }
 
 // ---------------------------------------------------------------- CG phases
-// Internal vectors (r, z, p0, p1, q) are [R][ldw] with ldw a multiple of 4;
-// the caller's b and x are [R][ldu].
+// Chronopoulos-Gear form of Jacobi-PCG (one reduction per iteration; same
+// iterates as the standard recurrence in exact arithmetic):
+//   r = b - M~x, u = D^-1 r, w = M~u, gamma = (r,u), delta = (w,u), alpha = gamma/delta, beta = 0
+//   repeat:  p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r,
+//            w = M~u, gamma' = (r,u), delta = (w,u), stop if ||r|| <= rtol ||b||,
+//            beta = gamma'/gamma, alpha = gamma' / (delta - beta gamma'/alpha)
+// The mass apply gathers a single vector (u).  Internal vectors (r FP64; u, w,
+// p, s in the dtype) are [R][ldw] with ldw a multiple of 4; the caller's b and
+// x are [R][ldu].
 template <typename T>
 struct CgVecs {
     const T* F;          // M~ fields (field 0 = diagonal)
@@ -164,49 +170,36 @@ struct CgVecs {
     const T* b;
     T* x;
     double* r;
-    T* z;
-    T* p0;
-    T* p1;
-    T* q;
+    T* u;
+    T* w;
+    T* p;
+    T* s;
     int N, m;
     long long ldw, ldu;
     long long ext_vec;   // R * ldw: extent of every internal vector
-    long long ext_user;  // R * ldu: extent of b and x
+    long long ext_user;  // extent of b and x
     long long ext_diag;  // extent of dinv
 };
 
-// z + beta p_old for four consecutive rows (coherent 16-byte loads)
-__device__ __forceinline__ float4 ld4c(const float* p) { return *reinterpret_cast<const float4*>(p); }
-template <int R>
-struct CombLoad4 {
-    const float* z;
-    const float* p;
-    long long ld;
-    float beta[R];
-    __device__ __forceinline__ float4 load4(int r, int idx) const {
-        const float b = beta[r];
-        return f4_fma(make_float4(b, b, b, b), ld4c(p + r * ld + idx), ld4c(z + r * ld + idx));
-    }
-    __device__ __forceinline__ float4 load4u(int r, int j) const {
-        const int off = j & 3;
-        const long long a = r * ld + (j - off);
-        const float b = beta[r];
-        const float4 bb = make_float4(b, b, b, b);
-        const float4 v0 = f4_fma(bb, ld4c(p + a), ld4c(z + a));
-        if (off == 0) return v0;
-        const float4 v1 = f4_fma(bb, ld4c(p + a + 4), ld4c(z + a + 4));
-        return f4_window(v0, v1, off);
-    }
-};
+// mass apply y = M~ vec for R vectors (interior rows on the fast path)
+template <int DIM, int P, typename T, int R, class Load>
+__device__ __forceinline__ void mass_apply_row(const CgVecs<T>& v, const Load& ld, int i, int dmax, const int* sdl,
+                                               T* acc, T* own) {
+    if (i >= dmax && i < v.N - dmax)
+        stencil_row_interior<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, sdl, acc, own);
+    else
+        stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+}
 
-// init: r = b - M~x, z = D^-1 r; partials (r,z), (r,r), (b,b)
+// init 1: r = b - M~x, u = D^-1 r; partials (r,u), (r,r), (b,b)
 template <int DIM, int P, typename T, int R>
-__device__ __forceinline__ void cg_init_rows(const CgVecs<T>& v, double* part) {
+__device__ __forceinline__ void cg_init1(const CgVecs<T>& v, double* part, const int* sdl) {
     for (int k = 0; k < 3 * R; ++k) part[k] = 0.0;
     PlainLoad<T> ld{v.x, v.ldu, v.ext_user};
+    const int dmax = max_delta<DIM, P>(v.m);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
-        stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
+        mass_apply_row<DIM, P, T, R>(v, ld, i, dmax, sdl, acc, own);
         const double di = IGA_IN(i, v.ext_diag, 6) ? (double)v.dinv[i] : 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -214,97 +207,42 @@ __device__ __forceinline__ void cg_init_rows(const CgVecs<T>& v, double* part) {
             const bool ok = IGA_IN(ou, v.ext_user, 7) && IGA_IN(ow, v.ext_vec, 16);
             const double bi = ok ? (double)v.b[ou] : 0.0;
             const double ri = bi - (double)acc[r];
-            const T zi = (T)(di * ri);
+            const T ui = (T)(di * ri);
             if (ok) {
                 v.r[ow] = ri;
-                v.z[ow] = zi;
+                v.u[ow] = ui;
             }
-            part[3 * r + 0] += ri * (double)zi;
+            part[3 * r + 0] += ri * (double)ui;
             part[3 * r + 1] += ri * ri;
             part[3 * r + 2] += bi * bi;
         }
     }
 }
 
-// phase A: p_new = z + beta p_old, q = M~ p_new; partial (p_new, q)
+// phase 2 (and init 2): w = M~u; partial (w,u)
 template <int DIM, int P, typename T, int R>
-__device__ __forceinline__ void cg_phase_a(const CgVecs<T>& v, const T* pold, T* pnew, const double* beta,
-                                           const int* active, double* part, const int* sdl) {
+__device__ __forceinline__ void cg_phase2(const CgVecs<T>& v, const int* active, double* part, const int* sdl) {
     for (int k = 0; k < R; ++k) part[k] = 0.0;
-    CombLoad<T, R> ld;
-    ld.z = v.z;
-    ld.p = pold;
-    ld.xs = v.ldw;
-    ld.ext = v.ext_vec;
+    PlainLoad<T> ld{v.u, v.ldw, v.ext_vec};
+    const int dmax = max_delta<DIM, P>(v.m);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
+        T acc[R], own[R];
+        mass_apply_row<DIM, P, T, R>(v, ld, i, dmax, sdl, acc, own);
 #pragma unroll
-    for (int r = 0; r < R; ++r) ld.beta[r] = (T)beta[r];
-    if constexpr (kCgFourRow && sizeof(T) == 4) {
-        // four rows per thread; interior groups vectorised (see stencil_row4)
-        CombLoad4<R> ld4;
-        ld4.z = v.z;
-        ld4.p = pold;
-        ld4.ld = v.ldw;
-#pragma unroll
-        for (int r = 0; r < R; ++r) ld4.beta[r] = (float)beta[r];
-        const int dmax = max_delta<DIM, P>(v.m);
-        const int ngroups = (v.N + 3) / 4;
-        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
-            const int i0 = 4 * g;
-            if (i0 >= dmax && i0 + 7 + dmax <= v.N - 1) {
-                float4 acc[R], own[R];
-                stencil_row4<DIM, P, true, R, kCgUnroll<R>>(v.F, v.pitch, ld4, i0, sdl, acc, own);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (!active[r]) continue;
-                    const long long o = (long long)r * v.ldw + i0;
-                    *reinterpret_cast<float4*>(pnew + o) = own[r];
-                    *reinterpret_cast<float4*>(v.q + o) = acc[r];
-                    part[r] += (double)own[r].x * acc[r].x + (double)own[r].y * acc[r].y +
-                               (double)own[r].z * acc[r].z + (double)own[r].w * acc[r].w;
-                }
-            } else {
-                for (int k = 0; k < 4 && i0 + k < v.N; ++k) {
-                    T acc[R], own[R];
-                    stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i0 + k, v.N, v.m, acc, own);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (!active[r]) continue;
-                        const long long o = (long long)r * v.ldw + i0 + k;
-                        if (IGA_IN(o, v.ext_vec, 8)) {
-                            pnew[o] = own[r];
-                            v.q[o] = acc[r];
-                        }
-                        part[r] += (double)own[r] * (double)acc[r];
-                    }
-                }
-            }
-        }
-    } else {
-        const int dmax = max_delta<DIM, P>(v.m);
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
-            T acc[R], own[R];
-            if (i >= dmax && i < v.N - dmax)
-                stencil_row_interior<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, sdl, acc, own);
-            else
-                stencil_row<DIM, P, T, true, R, kCgUnroll<R>>(v.F, v.pitch, ld, i, v.N, v.m, acc, own);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (!active[r]) continue;
-                const long long o = (long long)r * v.ldw + i;
-                if (IGA_IN(o, v.ext_vec, 8)) {
-                    pnew[o] = own[r];
-                    v.q[o] = acc[r];
-                }
-                part[r] += (double)own[r] * (double)acc[r];
-            }
+        for (int r = 0; r < R; ++r) {
+            if (!active[r]) continue;
+            const long long o = (long long)r * v.ldw + i;
+            if (IGA_IN(o, v.ext_vec, 8)) v.w[o] = acc[r];
+            part[r] += (double)own[r] * (double)acc[r];
         }
     }
 }
 
-// phase B: x += alpha p, r -= alpha q, z = D^-1 r; partials (r,z), (r,r)
+// phase 1: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r;
+// partials (r,u), (r,r)
 template <typename T, int R>
-__device__ __forceinline__ void cg_phase_b(const CgVecs<T>& v, const T* pnew, const double* alpha,
-                                           const int* active, double* part) {
+__device__ __forceinline__ void cg_phase1(const CgVecs<T>& v, const double* alpha, const double* beta,
+                                          const int* active, double* part) {
     for (int k = 0; k < 2 * R; ++k) part[k] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         const double di = IGA_IN(i, v.ext_diag, 9) ? (double)v.dinv[i] : 0.0;
@@ -314,13 +252,17 @@ __device__ __forceinline__ void cg_phase_b(const CgVecs<T>& v, const T* pnew, co
             const size_t o = (size_t)r * v.ldw + i;
             const size_t ou = (size_t)r * v.ldu + i;
             if (!IGA_IN(o, v.ext_vec, 10) || !IGA_IN(ou, v.ext_user, 17)) continue;
-            const T pi = pnew[o];
-            v.x[ou] = v.x[ou] + (T)alpha[r] * pi;
-            const double ri = v.r[o] - alpha[r] * (double)v.q[o];
-            const T zi = (T)(di * ri);
+            const T be = (T)beta[r], al = (T)alpha[r];
+            const T pi = v.u[o] + be * v.p[o];
+            const T si = v.w[o] + be * v.s[o];
+            v.p[o] = pi;
+            v.s[o] = si;
+            v.x[ou] = v.x[ou] + al * pi;
+            const double ri = v.r[o] - alpha[r] * (double)si;
+            const T ui = (T)(di * ri);
             v.r[o] = ri;
-            v.z[o] = zi;
-            part[2 * r + 0] += ri * (double)zi;
+            v.u[o] = ui;
+            part[2 * r + 0] += ri * (double)ui;
             part[2 * r + 1] += ri * ri;
         }
     }
@@ -330,7 +272,7 @@ struct CgCtl {
     double rtol;
     int max_it;
     int nblocks;
-    double* partials;    // [nblocks][3R]
+    double* partials;    // [nblocks][kCgStride(R)]
     unsigned* bar;       // [2]
     int* err;
     int* iters_out;      // [R]
@@ -339,37 +281,71 @@ struct CgCtl {
     int* status_acc;     // nullable: bit 8 set when an RHS misses rtol
 };
 
-// Partials of block b live at partials[b * 6R + ...]: phase A (p, q) at [0, R),
-// phase B (r, z), (r, r) at [R, 3R), initial (r, z), (r, r), (b, b) at [3R, 6R).
-// Separate regions make one barrier per phase sufficient: a block can only
-// overwrite a region after every block has passed the next barrier, i.e. after
-// every block has read that region.
+// Per-block partial layout (stride 10 R): phase-1 partials double-buffered by
+// iteration parity at [0, 2R) / [2R, 4R) (a fast block may write the next
+// iteration's phase-1 partials before a slow block has read the current ones),
+// phase-2 partials at [4R, 5R), init-1 partials at [6R, 9R).
+template <int R>
+constexpr int kCgStride = 10 * R;
+
+// Scalar update shared by the persistent and plain schedules (thread r of a block).
+__device__ __host__ inline void cg_scalars(double gamma_new, double rr, double delta, double rtol, double bnorm,
+                                           double& gamma, double& alpha, double& beta, int& active, int& iters,
+                                           double& rr_out, int* breakdown) {
+    iters += 1;
+    rr_out = rr;
+    if (rtol > 0.0 && sqrt(rr) <= rtol * bnorm) {
+        active = 0;
+        return;
+    }
+    const double b = gamma_new / gamma;
+    const double den = delta - b * gamma_new / alpha;
+    if (!(den > 0.0) || !isfinite(den)) {
+        active = 0;
+        *breakdown = 1;
+        return;
+    }
+    beta = b;
+    alpha = gamma_new / den;
+    gamma = gamma_new;
+}
+
 template <int DIM, int P, typename T, int R>
-__global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v, CgCtl c) {
+__global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) pcg_persistent_kernel(CgVecs<T> v, CgCtl c) {
     __shared__ double wsum[kCgWarps * 3 * R];
-    __shared__ double red[3 * R];
-    __shared__ double rz[R], rr[R], bnorm[R], alpha[R], beta[R];
+    __shared__ double red[3 * R], red2[R];
+    __shared__ double gam[R], rr[R], bnorm[R], alpha[R], beta[R];
     __shared__ int active[R], iters[R];
     __shared__ int sdl[StencilShape<DIM, P>::T0];
     double part[3 * R];
-    const int S = 6 * R;
+    constexpr int S = kCgStride<R>;
     fill_delta_table<DIM, P>(sdl, v.m);
 
-    cg_init_rows<DIM, P, T, R>(v, part);
+    cg_init1<DIM, P, T, R>(v, part, sdl);
     block_sum<3 * R>(part, wsum, red);
-    if (threadIdx.x < 3 * R && IGA_IN((long long)blockIdx.x * S + 3 * R + threadIdx.x, (long long)c.nblocks * S, 11))
-        c.partials[(size_t)blockIdx.x * S + 3 * R + threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x < 3 * R) c.partials[(size_t)blockIdx.x * S + 6 * R + threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x < R) active[threadIdx.x] = 1;
     if (!grid_barrier(c.bar, c.err)) return;
-    grid_sum<3 * R>(c.partials, gridDim.x, S, 3 * R, red);
+    cg_phase2<DIM, P, T, R>(v, active, part, sdl);
+    block_sum<R>(part, wsum, red);
+    if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
+    if (!grid_barrier(c.bar, c.err)) return;
+    grid_sum<3 * R>(c.partials, gridDim.x, S, 6 * R, red);
+    grid_sum<R>(c.partials, gridDim.x, S, 4 * R, red2);
     if (threadIdx.x < R) {
         const int r = threadIdx.x;
-        rz[r] = red[3 * r];
+        gam[r] = red[3 * r];
         rr[r] = red[3 * r + 1];
         bnorm[r] = sqrt(red[3 * r + 2]);
         beta[r] = 0.0;
-        alpha[r] = 0.0;
         iters[r] = 0;
         active[r] = bnorm[r] > 0.0 && !(c.rtol > 0.0 && sqrt(rr[r]) <= c.rtol * bnorm[r]);
+        const double d = red2[r];
+        if (active[r] && (!(d > 0.0) || !isfinite(d))) {
+            active[r] = 0;
+            atomicOr(c.err, 1);
+        }
+        alpha[r] = active[r] ? gam[r] / d : 0.0;
     }
     __syncthreads();
     // a zero right-hand side has the solution 0
@@ -377,46 +353,32 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
         if (!(bnorm[r] > 0.0))
             for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x)
                 if (IGA_IN((long long)r * v.ldu + i, v.ext_user, 15)) v.x[(size_t)r * v.ldu + i] = T(0);
-    // p_old starts at 0 (cleared by the host) so that p = z on the first iteration
     for (int it = 0; it < c.max_it; ++it) {
         bool any = false;
         for (int r = 0; r < R; ++r) any = any || active[r];
         if (!any) break;
-        T* pold = (it & 1) ? v.p1 : v.p0;
-        T* pnew = (it & 1) ? v.p0 : v.p1;
-        cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part, sdl);
-        block_sum<R>(part, wsum, red);
-        if (threadIdx.x < R && IGA_IN((long long)blockIdx.x * S + threadIdx.x, (long long)c.nblocks * S, 12))
-            c.partials[(size_t)blockIdx.x * S + threadIdx.x] = red[threadIdx.x];
-        if (!grid_barrier(c.bar, c.err)) return;
-        grid_sum<R>(c.partials, gridDim.x, S, 0, red);
-        if (threadIdx.x < R) {
-            const int r = threadIdx.x;
-            if (active[r]) {
-                const double pq = red[r];
-                if (!(pq > 0.0) || !isfinite(pq)) {
-                    active[r] = 0;
-                    if (blockIdx.x == 0) atomicOr(c.err, 1);
-                }
-                alpha[r] = active[r] ? rz[r] / pq : 0.0;
-            }
-        }
-        __syncthreads();
-        cg_phase_b<T, R>(v, pnew, alpha, active, part);
+        const int off1 = (it & 1) * 2 * R;
+        cg_phase1<T, R>(v, alpha, beta, active, part);
         block_sum<2 * R>(part, wsum, red);
-        if (threadIdx.x < 2 * R && IGA_IN((long long)blockIdx.x * S + R + threadIdx.x, (long long)c.nblocks * S, 13))
-            c.partials[(size_t)blockIdx.x * S + R + threadIdx.x] = red[threadIdx.x];
+        if (threadIdx.x < 2 * R) c.partials[(size_t)blockIdx.x * S + off1 + threadIdx.x] = red[threadIdx.x];
         if (!grid_barrier(c.bar, c.err)) return;
-        grid_sum<2 * R>(c.partials, gridDim.x, S, R, red);
+        cg_phase2<DIM, P, T, R>(v, active, part, sdl);
+        block_sum<R>(part, wsum, red);
+        if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
+        if (!grid_barrier(c.bar, c.err)) return;
+        grid_sum<2 * R>(c.partials, gridDim.x, S, off1, red);
+        grid_sum<R>(c.partials, gridDim.x, S, 4 * R, red2);
         if (threadIdx.x < R) {
             const int r = threadIdx.x;
             if (active[r]) {
-                const double rz_new = red[2 * r];
-                rr[r] = red[2 * r + 1];
-                beta[r] = rz_new / rz[r];
-                rz[r] = rz_new;
-                iters[r] += 1;
-                if (c.rtol > 0.0 && sqrt(rr[r]) <= c.rtol * bnorm[r]) active[r] = 0;
+                int brk = 0;
+                double rro = rr[r];
+                int act = active[r];
+                cg_scalars(red[2 * r], red[2 * r + 1], red2[r], c.rtol, bnorm[r], gam[r], alpha[r], beta[r], act,
+                           iters[r], rro, &brk);
+                active[r] = act;
+                rr[r] = rro;
+                if (brk && blockIdx.x == 0) atomicOr(c.err, 1);
             }
         }
         __syncthreads();
@@ -433,50 +395,47 @@ __global__ void __launch_bounds__(kCgThreads) pcg_persistent_kernel(CgVecs<T> v,
 
 // ---------------------------------------------------------------- plain schedule kernels
 template <int DIM, int P, typename T, int R>
-__global__ void __launch_bounds__(kCgThreads) cg_init_kernel(CgVecs<T> v, double* partials) {
+__global__ void __launch_bounds__(kCgThreads) cg_init1_kernel(CgVecs<T> v, double* partials) {
     __shared__ double wsum[kCgWarps * 3 * R];
     __shared__ double red[3 * R];
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
+    fill_delta_table<DIM, P>(sdl, v.m);
     double part[3 * R];
-    cg_init_rows<DIM, P, T, R>(v, part);
+    cg_init1<DIM, P, T, R>(v, part, sdl);
     block_sum<3 * R>(part, wsum, red);
-    if (threadIdx.x < 3 * R) partials[(size_t)blockIdx.x * 6 * R + 3 * R + threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x < 3 * R) partials[(size_t)blockIdx.x * kCgStride<R> + 6 * R + threadIdx.x] = red[threadIdx.x];
 }
 
 template <int DIM, int P, typename T, int R>
-__global__ void __launch_bounds__(kCgThreads) cg_a_kernel(CgVecs<T> v, const T* pold, T* pnew, const double* sc,
-                                                          double* partials) {
+__global__ void __launch_bounds__(kCgThreads) cg_phase2_kernel(CgVecs<T> v, const double* sc, double* partials) {
     __shared__ double wsum[kCgWarps * 3 * R];
     __shared__ double red[3 * R];
-    __shared__ double beta[R];
     __shared__ int active[R];
     __shared__ int sdl[StencilShape<DIM, P>::T0];
-    if (threadIdx.x < R) {
-        beta[threadIdx.x] = sc[threadIdx.x];
-        active[threadIdx.x] = (int)sc[2 * R + threadIdx.x];
-    }
+    if (threadIdx.x < R) active[threadIdx.x] = (int)sc[2 * R + threadIdx.x];
     fill_delta_table<DIM, P>(sdl, v.m);
     double part[3 * R];
-    cg_phase_a<DIM, P, T, R>(v, pold, pnew, beta, active, part, sdl);
+    cg_phase2<DIM, P, T, R>(v, active, part, sdl);
     block_sum<R>(part, wsum, red);
-    if (threadIdx.x < R) partials[(size_t)blockIdx.x * 6 * R + threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x < R) partials[(size_t)blockIdx.x * kCgStride<R> + 4 * R + threadIdx.x] = red[threadIdx.x];
 }
 
 template <typename T, int R>
-__global__ void __launch_bounds__(kCgThreads) cg_b_kernel(CgVecs<T> v, const T* pnew, const double* sc,
-                                                          double* partials) {
+__global__ void __launch_bounds__(kCgThreads) cg_phase1_kernel(CgVecs<T> v, const double* sc, double* partials) {
     __shared__ double wsum[kCgWarps * 3 * R];
     __shared__ double red[3 * R];
-    __shared__ double alpha[R];
+    __shared__ double alpha[R], beta[R];
     __shared__ int active[R];
     if (threadIdx.x < R) {
+        beta[threadIdx.x] = sc[threadIdx.x];
         alpha[threadIdx.x] = sc[R + threadIdx.x];
         active[threadIdx.x] = (int)sc[2 * R + threadIdx.x];
     }
     __syncthreads();
     double part[3 * R];
-    cg_phase_b<T, R>(v, pnew, alpha, active, part);
+    cg_phase1<T, R>(v, alpha, beta, active, part);
     block_sum<2 * R>(part, wsum, red);
-    if (threadIdx.x < 2 * R) partials[(size_t)blockIdx.x * 6 * R + R + threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x < 2 * R) partials[(size_t)blockIdx.x * kCgStride<R> + threadIdx.x] = red[threadIdx.x];
 }
 
 template <int K>
@@ -486,7 +445,7 @@ __global__ void grid_sum_kernel(const double* partials, int nblocks, int stride,
         double s = 0.0;
         for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * stride + off + k];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, off2);
         if (lane == 0) out[k] = s;
     }
 }
@@ -494,10 +453,10 @@ __global__ void grid_sum_kernel(const double* partials, int nblocks, int stride,
 // ---------------------------------------------------------------- host driver
 struct CgWork {
     double* r;
-    void* z;
-    void* p0;
-    void* p1;
-    void* q;
+    void* u;
+    void* w;
+    void* p;
+    void* s;
     double* partials;
     unsigned* bar;
     int* err;
@@ -517,11 +476,11 @@ static CgWork carve(void* base, long long N /* leading dimension of the internal
     };
     CgWork w;
     w.r = (double*)take(sizeof(double) * (size_t)R * N);
-    w.z = take(sizeof(T) * (size_t)R * N);
-    w.p0 = take(sizeof(T) * (size_t)R * N);
-    w.p1 = take(sizeof(T) * (size_t)R * N);
-    w.q = take(sizeof(T) * (size_t)R * N);
-    w.partials = (double*)take(sizeof(double) * (size_t)nblocks * 6 * R);
+    w.u = take(sizeof(T) * (size_t)R * N);
+    w.w = take(sizeof(T) * (size_t)R * N);
+    w.p = take(sizeof(T) * (size_t)R * N);
+    w.s = take(sizeof(T) * (size_t)R * N);
+    w.partials = (double*)take(sizeof(double) * (size_t)nblocks * 10 * R);
     w.bar = (unsigned*)take(64);
     w.err = (int*)take(64);
     w.iters = (int*)take(sizeof(int) * R);
@@ -533,8 +492,9 @@ static CgWork carve(void* base, long long N /* leading dimension of the internal
 
 static size_t carve_bytes(size_t es, long long N, int R, int nblocks) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    return up(sizeof(double) * (size_t)R * N) + 4 * up(es * (size_t)R * N) + up(sizeof(double) * (size_t)nblocks * 6 * R) +
-           2 * up(64) + up(sizeof(int) * R) + 3 * up(sizeof(double) * 3 * R) + 256;
+    return up(sizeof(double) * (size_t)R * N) + 4 * up(es * (size_t)R * N) +
+           up(sizeof(double) * (size_t)nblocks * 10 * R) + 2 * up(64) + up(sizeof(int) * R) +
+           3 * up(sizeof(double) * 3 * R) + 256;
 }
 
 template <int DIM, int P, typename T, int R>
@@ -566,10 +526,10 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
     v.b = b;
     v.x = x;
     v.r = w.r;
-    v.z = (T*)w.z;
-    v.p0 = (T*)w.p0;
-    v.p1 = (T*)w.p1;
-    v.q = (T*)w.q;
+    v.u = (T*)w.u;
+    v.w = (T*)w.w;
+    v.p = (T*)w.p;
+    v.s = (T*)w.s;
     v.N = (int)N;
     v.m = ops->m;
     v.ldw = ldw;
@@ -577,7 +537,9 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
     v.ext_vec = (long long)R * ldw;
     v.ext_user = (long long)(R - 1) * ldu + N;
     v.ext_diag = ops->pitch;
-    IGA_CUDA(cudaMemsetAsync(w.p0, 0, sizeof(T) * R * ldw, st));
+    // p and s start at 0 (beta = 0 on the first iteration multiplies them)
+    IGA_CUDA(cudaMemsetAsync(w.p, 0, sizeof(T) * R * ldw, st));
+    IGA_CUDA(cudaMemsetAsync(w.s, 0, sizeof(T) * R * ldw, st));
     IGA_CUDA(cudaMemsetAsync(w.bar, 0, 64, st));
     IGA_CUDA(cudaMemsetAsync(w.err, 0, 64, st));
     int iters[R];
@@ -621,62 +583,68 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
             if (err & 1) return fail(IGA_ERR_NONFINITE, "CG breakdown: (p, M p) <= 0 or non-finite");
         }
     } else {
-        // plain schedule: host-side scalars, two read-backs per iteration
+        // plain schedule: the same phases as separate launches, scalars on the host
         const int grid = nblocks;
-        cg_init_kernel<DIM, P, T, R><<<grid, kCgThreads, 0, st>>>(v, w.partials);
-        IGA_LAUNCH_CHECK("cg_init_kernel");
-        grid_sum_kernel<3 * R><<<1, kCgThreads, 0, st>>>(w.partials, grid, 6 * R, 3 * R, w.red);
-        IGA_LAUNCH_CHECK("grid_sum_kernel");
-        double red[3 * R], sc[3 * R];
-        IGA_CUDA(cudaMemcpyAsync(red, w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, st));
-        IGA_CUDA(cudaStreamSynchronize(st));
-        double rz[R], rr[R], bn[R];
+        constexpr int S = kCgStride<R>;
+        double red[3 * R], red2[R], sc[3 * R];
+        double gam[R], rr[R], bn[R], alpha[R], beta[R];
         int active[R];
         for (int r = 0; r < R; ++r) {
-            rz[r] = red[3 * r];
+            sc[r] = 0.0;
+            sc[R + r] = 0.0;
+            sc[2 * R + r] = 1.0;
+        }
+        cg_init1_kernel<DIM, P, T, R><<<grid, kCgThreads, 0, st>>>(v, w.partials);
+        IGA_LAUNCH_CHECK("cg_init1_kernel");
+        IGA_CUDA(cudaMemcpyAsync(w.sc, sc, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
+        cg_phase2_kernel<DIM, P, T, R><<<grid, kCgThreads, 0, st>>>(v, w.sc, w.partials);
+        IGA_LAUNCH_CHECK("cg_phase2_kernel");
+        grid_sum_kernel<3 * R><<<1, kCgThreads, 0, st>>>(w.partials, grid, S, 6 * R, w.red);
+        IGA_LAUNCH_CHECK("grid_sum_kernel");
+        IGA_CUDA(cudaMemcpyAsync(red, w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, st));
+        grid_sum_kernel<R><<<1, kCgThreads, 0, st>>>(w.partials, grid, S, 4 * R, w.red);
+        IGA_LAUNCH_CHECK("grid_sum_kernel");
+        IGA_CUDA(cudaMemcpyAsync(red2, w.red, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        IGA_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) {
+            gam[r] = red[3 * r];
             rr[r] = red[3 * r + 1];
             bn[r] = std::sqrt(red[3 * r + 2]);
+            beta[r] = 0.0;
             iters[r] = 0;
             active[r] = bn[r] > 0.0 && !(rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]);
-            sc[r] = 0.0;                // beta
-            sc[R + r] = 0.0;            // alpha
+            if (active[r] && (!(red2[r] > 0.0) || !std::isfinite(red2[r])))
+                return fail(IGA_ERR_NONFINITE, "CG breakdown: (u, M u) <= 0 or non-finite");
+            alpha[r] = active[r] ? gam[r] / red2[r] : 0.0;
             if (!(bn[r] > 0.0)) IGA_CUDA(cudaMemsetAsync(x + (size_t)r * ldu, 0, sizeof(T) * N, st));
         }
         for (int it = 0; it < max_it; ++it) {
             bool any = false;
             for (int r = 0; r < R; ++r) any = any || active[r];
             if (!any) break;
-            for (int r = 0; r < R; ++r) sc[2 * R + r] = active[r];
-            T* pold = (T*)((it & 1) ? w.p1 : w.p0);
-            T* pnew = (T*)((it & 1) ? w.p0 : w.p1);
-            IGA_CUDA(cudaMemcpyAsync(w.sc, sc, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
-            cg_a_kernel<DIM, P, T, R><<<grid, kCgThreads, 0, st>>>(v, pold, pnew, w.sc, w.partials);
-            IGA_LAUNCH_CHECK("cg_a_kernel");
-            grid_sum_kernel<R><<<1, kCgThreads, 0, st>>>(w.partials, grid, 6 * R, 0, w.red);
-            IGA_LAUNCH_CHECK("grid_sum_kernel");
-            IGA_CUDA(cudaMemcpyAsync(red, w.red, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-            IGA_CUDA(cudaStreamSynchronize(st));
             for (int r = 0; r < R; ++r) {
-                if (!active[r]) continue;
-                if (!(red[r] > 0.0) || !std::isfinite(red[r]))
-                    return fail(IGA_ERR_NONFINITE, "CG breakdown: (p, M p) <= 0 or non-finite");
-                sc[R + r] = rz[r] / red[r];
+                sc[r] = beta[r];
+                sc[R + r] = alpha[r];
+                sc[2 * R + r] = active[r];
             }
             IGA_CUDA(cudaMemcpyAsync(w.sc, sc, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
-            cg_b_kernel<T, R><<<grid, kCgThreads, 0, st>>>(v, pnew, w.sc, w.partials);
-            IGA_LAUNCH_CHECK("cg_b_kernel");
-            grid_sum_kernel<2 * R><<<1, kCgThreads, 0, st>>>(w.partials, grid, 6 * R, R, w.red);
+            cg_phase1_kernel<T, R><<<grid, kCgThreads, 0, st>>>(v, w.sc, w.partials);
+            IGA_LAUNCH_CHECK("cg_phase1_kernel");
+            cg_phase2_kernel<DIM, P, T, R><<<grid, kCgThreads, 0, st>>>(v, w.sc, w.partials);
+            IGA_LAUNCH_CHECK("cg_phase2_kernel");
+            grid_sum_kernel<2 * R><<<1, kCgThreads, 0, st>>>(w.partials, grid, S, 0, w.red);
             IGA_LAUNCH_CHECK("grid_sum_kernel");
             IGA_CUDA(cudaMemcpyAsync(red, w.red, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, st));
+            grid_sum_kernel<R><<<1, kCgThreads, 0, st>>>(w.partials, grid, S, 4 * R, w.red);
+            IGA_LAUNCH_CHECK("grid_sum_kernel");
+            IGA_CUDA(cudaMemcpyAsync(red2, w.red, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
             IGA_CUDA(cudaStreamSynchronize(st));
             for (int r = 0; r < R; ++r) {
                 if (!active[r]) continue;
-                const double rz_new = red[2 * r];
-                rr[r] = red[2 * r + 1];
-                sc[r] = rz_new / rz[r];
-                rz[r] = rz_new;
-                iters[r] += 1;
-                if (rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]) active[r] = 0;
+                int brk = 0;
+                cg_scalars(red[2 * r], red[2 * r + 1], red2[r], rtol, bn[r], gam[r], alpha[r], beta[r], active[r],
+                           iters[r], rr[r], &brk);
+                if (brk) return fail(IGA_ERR_NONFINITE, "CG breakdown: non-positive curvature or non-finite");
             }
         }
         long long tot = 0;
@@ -739,7 +707,7 @@ size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nb = std::max(1, sms) * kCgMaxBlocksPerSM;
-    return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, 4, nb);
+    return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, 4, nb);   // R = 4 is the largest chunk
 }
 
 int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long long ld, int nrhs, double rtol,
