@@ -259,6 +259,28 @@ typedef struct iga_wave_stats {
 int iga_wave_set_timing(iga_wave* wave, int on);
 int iga_wave_stats_get(const iga_wave* wave, iga_wave_stats* out);
 
+/* ---- batched persistent stepping -------------------------------------------
+ * A batch advances several FP32 waves (one mesh each, all with the same nshot
+ * in {1, 4, 8, 16} and the same dim / p; meshes of uneven size allowed) by
+ * nsteps leapfrog steps in ONE cooperative persistent launch: the grid is split
+ * into one block partition per wave, each partition runs its own force, CG
+ * (Chronopoulos-Gear Jacobi-PCG, per-shot convergence, bounded partition
+ * barriers) and update for every step.  The waves keep owning their state,
+ * traces and counters (wave_get_state / wave_traces work as usual).
+ * use_graph = 1 captures the launch in a CUDA graph on first use and replays it
+ * (the step counters live in device memory).  The batch borrows the waves: they
+ * must outlive it.  Synchronous (reads back the status word). */
+typedef struct iga_batch iga_batch;
+int iga_batch_create(int nprob, iga_wave* const* waves, iga_batch** out);
+int iga_batch_destroy(iga_batch* batch);
+int iga_batch_step(iga_batch* batch, int nsteps, int use_graph, void* stream);
+/* Tuner of the block partition: `rounds` trial launches of trial_steps steps
+ * each (the waves advance; reset them afterwards), rescaling each partition's
+ * share by its measured time so that all partitions finish together. */
+int iga_batch_tune(iga_batch* batch, int trial_steps, int rounds, void* stream);
+/* Blocks per partition (host array of nprob ints). */
+int iga_batch_partition(const iga_batch* batch, int* blocks_out);
+
 /* ---- adjoint ------------------------------------------------------------
  * wave_adjoint: restarts the wave (FP64 only) from its initial condition, runs
  * nsteps leapfrog steps with checkpoints (u^n, u^{n-1}, a^{n-1}) every

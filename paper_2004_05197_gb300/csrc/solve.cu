@@ -30,6 +30,7 @@
 #include "host_bspline.h"
 #include "iga_internal.cuh"
 #include "stencil.cuh"
+#include "cg.cuh"
 
 namespace iga {
 
@@ -55,7 +56,6 @@ constexpr int kCgMaxBlocksPerSM = 2;
 template <int R>
 constexpr int kCgUnroll = R >= 4 ? 2 : 4;   // fields in flight per thread in the mass apply
 constexpr int kCgWarps = kCgThreads / 32;
-constexpr long long kBarrierSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------- loaders
 // Vectors written inside the persistent kernel are read with ordinary
@@ -84,27 +84,6 @@ struct CombLoad {   // z + beta p_old, formed on the fly
     }
 };
 
-// ---------------------------------------------------------------- reductions
-// Block sum of K doubles per thread (v[K]) into red[K] (shared), fixed order.
-template <int K>
-__device__ __forceinline__ void block_sum(double* v, double* wsum /*[kCgWarps][K]*/, double* red /*[K]*/) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double s = v[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) wsum[w * K + k] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double s = 0.0;
-        for (int ww = 0; ww < kCgWarps; ++ww) s += wsum[ww * K + k];
-        red[k] = s;
-    }
-    __syncthreads();
-}
-
 // Sum over blocks of partials[b * stride + off + k] (k < K) into out[k]
 // (shared), fixed order; every block computes the identical result.
 template <int K>
@@ -121,35 +100,6 @@ __device__ __forceinline__ void grid_sum(const double* partials, int nblocks, in
         if (lane == 0) out[k] = s;
     }
     __syncthreads();
-}
-
-// Bounded grid barrier (cooperative launch guarantees co-residency).  On time-out
-// it sets bit 4 of *err and returns false; every caller then leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*vgen == gen) {
-                __nanosleep(32);
-                if (clock64() - t0 > kBarrierSpinCycles) {
-                    atomicOr(err, 4);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *((volatile int*)err) == 0;
 }
 
 // ---------------------------------------------------------------- CG phases
@@ -294,28 +244,6 @@ struct CgCtl {
 template <int R>
 constexpr int kCgStride = 10 * R;
 
-// Scalar update shared by the persistent and plain schedules (thread r of a block).
-__device__ __host__ inline void cg_scalars(double gamma_new, double rr, double delta, double rtol, double bnorm,
-                                           double& gamma, double& alpha, double& beta, int& active, int& iters,
-                                           double& rr_out, int* breakdown) {
-    iters += 1;
-    rr_out = rr;
-    if (rtol > 0.0 && sqrt(rr) <= rtol * bnorm) {
-        active = 0;
-        return;
-    }
-    const double b = gamma_new / gamma;
-    const double den = delta - b * gamma_new / alpha;
-    if (!(den > 0.0) || !isfinite(den)) {
-        active = 0;
-        *breakdown = 1;
-        return;
-    }
-    beta = b;
-    alpha = gamma_new / den;
-    gamma = gamma_new;
-}
-
 template <int DIM, int P, typename T, int R>
 __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) pcg_persistent_kernel(CgVecs<T> v, CgCtl c) {
     __shared__ double wsum[kCgWarps * 3 * R];
@@ -328,14 +256,14 @@ __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) 
     fill_delta_table<DIM, P>(sdl, v.m);
 
     cg_init1<DIM, P, T, R>(v, part, sdl);
-    block_sum<3 * R>(part, wsum, red);
+    block_sum<3 * R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < 3 * R) c.partials[(size_t)blockIdx.x * S + 6 * R + threadIdx.x] = red[threadIdx.x];
     if (threadIdx.x < R) active[threadIdx.x] = 1;
-    if (!grid_barrier(c.bar, c.err)) return;
+    if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
     cg_phase2<DIM, P, T, R>(v, active, part, sdl);
-    block_sum<R>(part, wsum, red);
+    block_sum<R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
-    if (!grid_barrier(c.bar, c.err)) return;
+    if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
     grid_sum<3 * R>(c.partials, gridDim.x, S, 6 * R, red);
     grid_sum<R>(c.partials, gridDim.x, S, 4 * R, red2);
     if (threadIdx.x < R) {
@@ -365,13 +293,13 @@ __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) 
         if (!any) break;
         const int off1 = (it & 1) * 2 * R;
         cg_phase1<T, R>(v, alpha, beta, active, part);
-        block_sum<2 * R>(part, wsum, red);
+        block_sum<2 * R, kCgWarps>(part, wsum, red);
         if (threadIdx.x < 2 * R) c.partials[(size_t)blockIdx.x * S + off1 + threadIdx.x] = red[threadIdx.x];
-        if (!grid_barrier(c.bar, c.err)) return;
+        if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
         cg_phase2<DIM, P, T, R>(v, active, part, sdl);
-        block_sum<R>(part, wsum, red);
+        block_sum<R, kCgWarps>(part, wsum, red);
         if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
-        if (!grid_barrier(c.bar, c.err)) return;
+        if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
         grid_sum<2 * R>(c.partials, gridDim.x, S, off1, red);
         grid_sum<R>(c.partials, gridDim.x, S, 4 * R, red2);
         if (threadIdx.x < R) {
@@ -408,7 +336,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_init1_kernel(CgVecs<T> v, doubl
     fill_delta_table<DIM, P>(sdl, v.m);
     double part[3 * R];
     cg_init1<DIM, P, T, R>(v, part, sdl);
-    block_sum<3 * R>(part, wsum, red);
+    block_sum<3 * R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < 3 * R) partials[(size_t)blockIdx.x * kCgStride<R> + 6 * R + threadIdx.x] = red[threadIdx.x];
 }
 
@@ -422,7 +350,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_phase2_kernel(CgVecs<T> v, cons
     fill_delta_table<DIM, P>(sdl, v.m);
     double part[3 * R];
     cg_phase2<DIM, P, T, R>(v, active, part, sdl);
-    block_sum<R>(part, wsum, red);
+    block_sum<R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < R) partials[(size_t)blockIdx.x * kCgStride<R> + 4 * R + threadIdx.x] = red[threadIdx.x];
 }
 
@@ -440,7 +368,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_phase1_kernel(CgVecs<T> v, cons
     __syncthreads();
     double part[3 * R];
     cg_phase1<T, R>(v, alpha, beta, active, part);
-    block_sum<2 * R>(part, wsum, red);
+    block_sum<2 * R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < 2 * R) partials[(size_t)blockIdx.x * kCgStride<R> + threadIdx.x] = red[threadIdx.x];
 }
 

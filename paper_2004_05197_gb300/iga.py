@@ -37,6 +37,7 @@ EXPORTED = [
     "iga_wave_destroy", "iga_wave_step", "iga_wave_get_state", "iga_wave_traces",
     "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count", "iga_wave_reset",
     "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum", "iga_wave_adjoint",
+    "iga_batch_create", "iga_batch_destroy", "iga_batch_step", "iga_batch_tune", "iga_batch_partition",
 ]
 
 
@@ -107,6 +108,11 @@ _sig = {
     "iga_wave_stats_get": [_vp, C.POINTER(iga_wave_stats)],
     "iga_ops_spectrum": [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), _vp],
     "iga_wave_adjoint": [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), _vp],
+    "iga_batch_create": [_i, C.POINTER(_vp), C.POINTER(_vp)],
+    "iga_batch_destroy": [_vp],
+    "iga_batch_step": [_vp, _i, _i, _vp],
+    "iga_batch_tune": [_vp, _i, _i, _vp],
+    "iga_batch_partition": [_vp, C.POINTER(_i)],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -302,3 +308,28 @@ def iga_wave_adjoint(wave, nsteps, checkpoint_every, obs, n_theta_total=0, strea
     _check(_lib.iga_wave_adjoint(wave, nsteps, checkpoint_every, obs_p, C.byref(J), gp, _stream(stream)))
     del obs_a
     return J.value, grad
+
+
+def iga_batch_create(waves):
+    arr = (C.c_void_p * len(waves))(*[w.value if isinstance(w, C.c_void_p) else w for w in waves])
+    out = C.c_void_p()
+    _check(_lib.iga_batch_create(len(waves), arr, C.byref(out)))
+    return out
+
+
+def iga_batch_destroy(batch):
+    _check(_lib.iga_batch_destroy(batch))
+
+
+def iga_batch_step(batch, nsteps, use_graph=True, stream=None):
+    _check(_lib.iga_batch_step(batch, nsteps, 1 if use_graph else 0, _stream(stream)))
+
+
+def iga_batch_tune(batch, trial_steps=5, rounds=3, stream=None):
+    _check(_lib.iga_batch_tune(batch, trial_steps, rounds, _stream(stream)))
+
+
+def iga_batch_partition(batch, nprob):
+    buf = (C.c_int * nprob)()
+    _check(_lib.iga_batch_partition(batch, buf))
+    return list(buf)
