@@ -131,12 +131,9 @@ struct CgVecs {
     long long ext_diag;  // extent of dinv
 };
 
-// Rows of this block: an equal contiguous share [row0(b), row0(b+1)) per block, so
-// every block does the same work between two grid barriers.
-__device__ __forceinline__ int cg_row0(int N, int next = 0) {
-    return (int)(((long long)N * (blockIdx.x + next)) / gridDim.x);
-}
-
+// Rows are distributed grid-stride: in each round all blocks cover one
+// contiguous window, so the mirrored field reads F_u[i - Delta] hit L2 (a
+// contiguous range per block was measured to raise DRAM reads by 27 %).
 // mass apply y = M~ vec for R vectors (interior rows on the fast path)
 template <int DIM, int P, typename T, int R, class Load>
 __device__ __forceinline__ void mass_apply_row(const CgVecs<T>& v, const Load& ld, int i, int dmax, const int* sdl,
@@ -153,7 +150,7 @@ __device__ __forceinline__ void cg_init1(const CgVecs<T>& v, double* part, const
     for (int k = 0; k < 3 * R; ++k) part[k] = 0.0;
     PlainLoad<T> ld{v.x, v.ldu, v.ext_user};
     const int dmax = max_delta<DIM, P>(v.m);
-    for (int i = cg_row0(v.N) + threadIdx.x, i1 = cg_row0(v.N, 1); i < i1; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
         mass_apply_row<DIM, P, T, R>(v, ld, i, dmax, sdl, acc, own);
         const double di = IGA_IN(i, v.ext_diag, 6) ? (double)v.dinv[i] : 0.0;
@@ -181,7 +178,7 @@ __device__ __forceinline__ void cg_phase2(const CgVecs<T>& v, const int* active,
     for (int k = 0; k < R; ++k) part[k] = 0.0;
     PlainLoad<T> ld{v.u, v.ldw, v.ext_vec};
     const int dmax = max_delta<DIM, P>(v.m);
-    for (int i = cg_row0(v.N) + threadIdx.x, i1 = cg_row0(v.N, 1); i < i1; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
         mass_apply_row<DIM, P, T, R>(v, ld, i, dmax, sdl, acc, own);
 #pragma unroll
@@ -200,7 +197,7 @@ template <typename T, int R>
 __device__ __forceinline__ void cg_phase1(const CgVecs<T>& v, const double* alpha, const double* beta,
                                           const int* active, double* part) {
     for (int k = 0; k < 2 * R; ++k) part[k] = 0.0;
-    for (int i = cg_row0(v.N) + threadIdx.x, i1 = cg_row0(v.N, 1); i < i1; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         const double di = IGA_IN(i, v.ext_diag, 9) ? (double)v.dinv[i] : 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -285,7 +282,7 @@ __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) 
     // a zero right-hand side has the solution 0
     for (int r = 0; r < R; ++r)
         if (!(bnorm[r] > 0.0))
-            for (int i = cg_row0(v.N) + threadIdx.x, i1 = cg_row0(v.N, 1); i < i1; i += blockDim.x)
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x)
                 if (IGA_IN((long long)r * v.ldu + i, v.ext_user, 15)) v.x[(size_t)r * v.ldu + i] = T(0);
     for (int it = 0; it < c.max_it; ++it) {
         bool any = false;
