@@ -398,6 +398,7 @@ def main():
     ap.add_argument("--oracle-rows", type=int, default=200)
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison leg")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -417,8 +418,10 @@ def main():
     __graft_entry__.build()
     out, ctx = run_ours(args, rank, world, device)
     if rank == 0:
-        out["components"].update(fp64_plain_and_error(ctx, args))
-        out["e2e"] = run_e2e(args, ctx)
+        if not args.no_compare:
+            out["components"].update(fp64_plain_and_error(ctx, args))
+        if args.e2e_steps > 0:
+            out["e2e"] = run_e2e(args, ctx)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(args)
     if world > 1:
