@@ -310,6 +310,101 @@ def run_e2e(args, ctx):
             "d2h_bytes_per_step": int(d2h), "s_per_step": t}
 
 
+def run_batched(args):
+    """Batched FP32 form vs the plain FP64 single-shot form (the batched workload).
+
+    Four 2-D p=3 quarter-annulus meshes, 128^2, 256^2, 384^2, 512^2 elements
+    (c = 1 + 0.5 sin(2 pi x) cos(2 pi y), q = 3, M = 8, dt = 0.1 h), 16 Ricker shots
+    each at seeded uniform positions in [0.1, 0.9]^2: 64 shots advanced together
+    in one persistent cooperative launch replayed from a CUDA graph (16 shots per
+    mesh as two right-hand-side groups of 8).  The plain form runs one shot at a
+    time in FP64 with the non-persistent CG schedule; its rate is measured on a
+    few steps per mesh and the error of the FP32 batch against FP64 is taken on
+    the same window.
+    """
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300 import workloads as W
+    sizes = (128, 256, 384, 512)
+    nsteps = args.batched_steps
+    meshes, waves = [], []
+    for k, n in enumerate(sizes):
+        w = W.scaled("annulus512_p3", n_el=n)
+        sp = W.make_space(w)
+        ops = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
+        src = inputs.shot_positions(16, dim=2, seed=inputs.SEED_SHOTS_2D + 100 * k)
+        meshes.append((w, sp, ops, src))
+        for g in range(2):
+            waves.append(iga.iga_wave_create(ops, 8, iga.IGA_F32, W.dt_of(w), src_pos=src[8 * g:8 * g + 8],
+                                             f0=10.0, t0=0.1, rec_pos=np.array([[0.5, 0.5]]), nsteps_max=nsteps + 64,
+                                             cg_rtol=args.cg_rtol, cg_max_it=args.cg_max_it, cfl_check=2))
+    b = iga.iga_batch_create(waves)
+    iga.iga_batch_tune(b, trial_steps=5, rounds=3)
+    part = iga.iga_batch_partition(b, len(waves))
+    for wv, k in zip(waves, range(len(waves))):
+        iga.iga_wave_reset(wv, meshes[k // 2][2])
+    iga.iga_batch_step(b, nsteps, use_graph=True)      # capture + warm-up
+    for wv, k in zip(waves, range(len(waves))):
+        iga.iga_wave_reset(wv, meshes[k // 2][2])
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    iga.iga_batch_step(b, nsteps, use_graph=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    batched = 64 * nsteps / (ms / 1e3)
+    # FP32 states of the first shot of each mesh after nsteps, for the error
+    u32 = []
+    for k, (w, sp, ops, src) in enumerate(meshes):
+        N = iga.iga_ops_info_get(ops).N
+        u = torch.empty((8, N), dtype=torch.float32, device="cuda")
+        iga.iga_wave_get_state(waves[2 * k], u)
+        u32.append(u[0].double().cpu().numpy())
+    iga.iga_batch_destroy(b)
+    for wv in waves:
+        iga.iga_wave_destroy(wv)
+    # plain FP64 single-shot schedule (first shot of each mesh) timed on `plain_steps`
+    # steps; the FP64 reference for the error is the same shot run for all steps with
+    # the persistent FP64 solver (same arithmetic, CG rtol 1e-10)
+    plain_t, plain_ss, errs = 0.0, 0, []
+    for k, (w, sp, ops, src) in enumerate(meshes):
+        wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
+                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN,
+                                 cfl_check=0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        iga.iga_wave_step(wv, args.plain_steps)
+        torch.cuda.synchronize()
+        plain_t += time.perf_counter() - t
+        plain_ss += args.plain_steps
+        iga.iga_wave_destroy(wv)
+        wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
+                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, cfl_check=0)
+        iga.iga_wave_step(wv, nsteps)
+        N = iga.iga_ops_info_get(ops).N
+        u = torch.empty((1, N), dtype=torch.float64, device="cuda")
+        iga.iga_wave_get_state(wv, u)
+        torch.cuda.synchronize()
+        ref = u[0].cpu().numpy()
+        errs.append(float(np.linalg.norm(u32[k] - ref) / max(np.linalg.norm(ref), 1e-300)))
+        iga.iga_wave_destroy(wv)
+    for (w, sp, ops, src) in meshes:
+        iga.iga_ops_destroy(ops)
+        iga.iga_space_destroy(sp)
+    # a plain shot-step costs the same whichever shot it is: the mean over the four meshes
+    plain = plain_ss / plain_t
+    return {"batched_workload": "annulus p=3 meshes 128^2,256^2,384^2,512^2 x 16 Ricker shots, %d steps" % nsteps,
+            "batched_fp32_shot_steps_per_s": batched, "batched_ms": ms,
+            "plain_fp64_single_shot_shot_steps_per_s": plain,
+            "batched_over_plain": batched / plain,
+            "batched_fp32_vs_fp64_rel_l2_error_max": max(errs),
+            "batched_partition_blocks": part}
+
+
 # ------------------------------------------------------------------ oracle legs
 def oracle_sample(args, budget_s=20.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload.
@@ -399,6 +494,9 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-mesh leg")
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--plain-steps", type=int, default=5)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -422,6 +520,8 @@ def main():
             out["components"].update(fp64_plain_and_error(ctx, args))
         if args.e2e_steps > 0:
             out["e2e"] = run_e2e(args, ctx)
+        if not args.no_batched:
+            out["components"].update(run_batched(args))
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(args)
     if world > 1:
