@@ -97,14 +97,16 @@ class ClockSampler:
 
 
 def cg_bytes(nM, R, es):
-    """Algorithmic HBM bytes per row of one persistent PCG launch (fields once per pass).
+    """Algorithmic HBM bytes per row of one persistent PCG launch (Chronopoulos-Gear
+    form; every field element read once per mass apply).
 
-    init : fields nM*es + D^-1 es + per RHS (x, b, z: es each; r: 8)
-    iter : phase A fields nM*es + per RHS (z, p_old read; p_new, q write: 4 es)
-           phase B D^-1 es + per RHS (p_new, q, x read, x, z write: 5 es; r read+write: 16)
+    init : apply r = b - M~x: fields nM*es + D^-1 es + per RHS (x, b read, u write: 3 es;
+           r write: 8); apply w = M~u: fields nM*es + per RHS (u read, w write: 2 es)
+    iter : phase 1 D^-1 es + per RHS (u, w, p, s, x read, p, s, x, u write: 9 es;
+           r read + write: 16); phase 2 w = M~u: fields nM*es + per RHS (u read, w write: 2 es)
     """
-    init = nM * es + es + R * (3 * es + 8)
-    it = nM * es + es + R * (9 * es + 16)
+    init = 2 * nM * es + es + R * (5 * es + 8)
+    it = nM * es + es + R * (11 * es + 16)
     return init, it
 
 
@@ -406,20 +408,25 @@ def run_batched(args):
 
 
 # ------------------------------------------------------------------ oracle legs
-def oracle_sample(args, budget_s=20.0):
+def oracle_sample(args):
     """The FP64 oracle, as it stands, on a bounded sample of the workload.
 
-    (a) surrogate assembly: the oracle's Surrogate() (true rows at every sample
-        row, interpolation) plus surrogate rows of a random subset of the
-        workload's rows -> seconds per row;
-    (b) leapfrog: oracle steps on the same workload family at n_el = 12
-        (same p, q, M rule, map and coefficient) -> seconds per row per step.
-    Both are scaled to the full workload (per-row costs times N) and combined
-    into shot-steps/s of one full pass.
+    The oracle's assembly of the full workload is true quadrature of every sample
+    row (Surrogate()) plus, for every row, true quadrature and surrogate
+    evaluation (Surrogate.rows()).  Sampled here:
+    (a) true_rows() of `oracle_rows` random sample rows and of `oracle_rows`
+        random rows of the full workload -> seconds per quadrated row;
+    (b) Surrogate() and Surrogate.rows() of the n_el = 24 version (same p, q, M,
+        map, coefficient) on `oracle_rows` rows, minus their true_rows() time ->
+        seconds of interpolation and evaluation per row;
+    (c) leapfrog: oracle steps of the n_el = 12 version -> seconds per row per step.
+    All per-row costs are scaled to the full workload's counts and combined into
+    shot-steps/s of one full pass.
     """
     import numpy as np
 
-    import inputs
+    from oracle.assembly import true_rows
+    from oracle.surrogate import Surrogate, sample_indices
     from oracle.wave import Leapfrog
     from paper_2004_05197_gb300 import workloads as W
     from tests.oracle_cases import oracle_space, oracle_surrogate
@@ -427,17 +434,39 @@ def oracle_sample(args, budget_s=20.0):
     nsteps = args.nsteps or w["steps"]
     sp = oracle_space(w)
     N = sp.N
-    t = time.perf_counter()
-    from oracle.surrogate import Surrogate
-    S = Surrogate(sp, w["q"], w["M"])
-    t_build = time.perf_counter() - t
     rng = np.random.default_rng(0)
-    nrows = args.oracle_rows
-    rows = sp.multi(rng.integers(0, N, size=nrows))
+    k = args.oracle_rows
+    samp = sample_indices(sp.m, sp.p, w["M"])
+    n_sample_rows = len(samp) ** sp.dim
+    srows = np.stack([rng.choice(samp, k) for _ in range(sp.dim)], axis=1)
     t = time.perf_counter()
-    S.rows(rows)
+    true_rows(sp, srows)
+    t_srows = time.perf_counter() - t
+    rows = sp.multi(rng.integers(0, N, size=k))
+    t = time.perf_counter()
+    true_rows(sp, rows)
     t_rows = time.perf_counter() - t
-    asm_s = t_build + N * t_rows / nrows
+    wm = W.scaled(args.workload, n_el=24)
+    spm = oracle_space(wm)
+    rows_m = spm.multi(rng.integers(0, spm.N, size=k))
+    t = time.perf_counter()
+    Sm = Surrogate(spm, wm["q"], wm["M"])
+    t_build_m = time.perf_counter() - t
+    t = time.perf_counter()
+    Sm.rows(rows_m)
+    t_srow_m = time.perf_counter() - t
+    t = time.perf_counter()
+    true_rows(spm, rows_m)
+    t_true_m = time.perf_counter() - t
+    n_samp_m = len(Sm.samp) ** spm.dim
+    ks = min(k, n_samp_m)
+    srows_m = np.stack([rng.choice(Sm.samp, ks) for _ in range(spm.dim)], axis=1)
+    t = time.perf_counter()
+    true_rows(spm, srows_m)
+    t_samp_m = (time.perf_counter() - t) * n_samp_m / ks           # sample quadrature inside Surrogate()
+    eval_s = max(t_srow_m - t_true_m, 0.0) / k                     # evaluation per row
+    interp_s = max(t_build_m - t_samp_m, 0.0)                       # interpolation (tiny)
+    asm_s = n_sample_rows * t_srows / k + interp_s + N * (t_rows / k + eval_s)
     ws = W.scaled(args.workload, n_el=12, M=2)
     sps, Ss = oracle_surrogate(ws)
     SK, SM = Ss.rows(sps.all_rows())
@@ -449,12 +478,15 @@ def oracle_sample(args, budget_s=20.0):
     t_small = time.perf_counter() - t
     step_s = t_small / steps_small * N / sps.N
     total = asm_s + nsteps * step_s
+    sample_s = t_srows + t_rows + t_build_m + t_srow_m + t_true_m + t_small
     return {"value": args.nshot * nsteps / total, "unit": "shot-steps/s", "cores": 1, "kind": "oracle",
-            "sample": ("oracle surrogate assembly of the full workload's sample rows plus %d random rows "
-                       "(%.1f s, scaled by N=%d), and %d oracle leapfrog steps of the n_el=12 version "
-                       "(%.1f s, scaled by N); full pass estimated at %.0f s" % (
-                           nrows, t_build + t_rows, N, steps_small, t_small, total)),
-            "surrogate_rows_per_s": N / asm_s, "sample_seconds": t_build + t_rows + t_small}
+            "sample": ("oracle true-row quadrature of %d random sample rows and %d random rows of the full "
+                       "workload (%.1f s; scaled to %d sample rows and N=%d rows), surrogate interpolation "
+                       "and evaluation of %d rows of the n_el=24 version (%.1f s; scaled by N), and %d "
+                       "oracle leapfrog steps of the n_el=12 version (%.1f s; scaled by N); full pass "
+                       "estimated at %.0f s" % (k, k, t_srows + t_rows, n_sample_rows, N, k,
+                                               t_build_m + t_srow_m + t_true_m, steps_small, t_small, total)),
+            "surrogate_rows_per_s": N / asm_s, "sample_seconds": sample_s}
 
 
 def run_reference(args):
@@ -490,7 +522,7 @@ def main():
     ap.add_argument("--cg-max-it", type=int, default=2000)
     ap.add_argument("--compare-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--oracle-rows", type=int, default=200)
+    ap.add_argument("--oracle-rows", type=int, default=96)
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison leg")
