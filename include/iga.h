@@ -186,6 +186,31 @@ int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nr
                    double rtol, int max_it, unsigned flags, int* iters_out,
                    double* relres_out, void* stream);
 
+/* mass_solve_noalloc: the paper has no counterpart to this entry point; it is
+ * an operational variant of iga_mass_solve.  Same arguments, solver, results
+ * and return codes, but no device memory is allocated: the CG workspace is a
+ * fixed array of IGA_NOALLOC_SCRATCH_BYTES compiled into the library instead
+ * of a buffer the library cudaMallocs on first use.  It is for callers that
+ * cannot have the library allocate: cudaMalloc / cudaFree may synchronise the
+ * whole device and stall the caller's other streams inside a latency-bound
+ * loop, and a caller whose device memory is managed by another allocator (a
+ * framework's caching allocator, a fixed memory budget) needs the library's
+ * footprint known up front.
+ * Limit: the workspace for (N, dtype, nrhs) must fit in the array.  It is
+ * about 40 N bytes for FP64 with nrhs < 4 and 160 N with nrhs >= 4 (FP32:
+ * 24 N and 96 N), plus ~100 KB; e.g. FP64 single-RHS solves up to about
+ * 1.6 M rows.  Larger requests return IGA_ERR_ARG before any work.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, which may load the module holding it) with that
+ * device current; make that first call before any stream capture.
+ * Sharing: all calls on a device use the same array, so calls that overlap in
+ * time (different streams or host threads) race and corrupt one another;
+ * the caller must serialise them (e.g. one stream). */
+#define IGA_NOALLOC_SCRATCH_BYTES (64u << 20)
+int iga_mass_solve_noalloc(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs,
+                           double rtol, int max_it, unsigned flags, int* iters_out,
+                           double* relres_out, void* stream);
+
 /* ---- spectrum --------------------------------------------------------------
  * Extreme eigenvalues of the pencil K~ v = lambda M~ v by k Lanczos steps in the
  * M~ inner product (each step: one K~ apply, one mass solve, one M~ apply).

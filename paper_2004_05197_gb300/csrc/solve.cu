@@ -641,6 +641,16 @@ size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
     return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, 4, nb);   // R = 4 is the largest chunk
 }
 
+// Workspace for exactly the chunks pcg_typed runs for nrhs right-hand sides
+// (4-wide chunks while at least 4 remain, then single ones).
+size_t mass_solve_work_bytes_nrhs(const iga_ops* ops, int dtype, int nrhs) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nb = std::max(1, sms) * kCgMaxBlocksPerSM;
+    return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, nrhs >= 4 ? 4 : 1, nb);
+}
+
 int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long long ld, int nrhs, double rtol,
                     int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st, void* work,
                     size_t work_bytes, long long* iter_acc, int* status_acc) {

@@ -38,6 +38,7 @@ EXPORTED = [
     "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count", "iga_wave_reset",
     "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum", "iga_wave_adjoint",
     "iga_batch_create", "iga_batch_destroy", "iga_batch_step", "iga_batch_tune", "iga_batch_partition",
+    "iga_mass_solve_noalloc",
 ]
 
 
@@ -97,6 +98,7 @@ _sig = {
     "iga_ops_sample_indices": [_vp, C.POINTER(_i)],
     "iga_stencil_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
     "iga_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
+    "iga_mass_solve_noalloc": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_wave_create": [_vp, C.POINTER(iga_wave_desc), C.POINTER(_vp)],
     "iga_wave_destroy": [_vp],
     "iga_wave_step": [_vp, _i, _vp],
@@ -226,6 +228,22 @@ def iga_mass_solve(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_stats=Tru
     ok = (IGA_OK, IGA_ERR_NOT_CONVERGED) if allow_not_converged else (IGA_OK,)
     rc = _check(_lib.iga_mass_solve(ops, dtype, _dptr(b), _dptr(x), nrhs, rtol, max_it, flags,
                                     iters, rel, _stream(stream)), ok)
+    if want_stats:
+        return rc, np.array(iters[:]), np.array(rel[:])
+    return rc, None, None
+
+
+IGA_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def iga_mass_solve_noalloc(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_stats=True, stream=None,
+                           allow_not_converged=False):
+    """iga_mass_solve with the CG workspace in the library's fixed device array (no allocation)."""
+    iters = (C.c_int * nrhs)() if want_stats else None
+    rel = (C.c_double * nrhs)() if want_stats else None
+    ok = (IGA_OK, IGA_ERR_NOT_CONVERGED) if allow_not_converged else (IGA_OK,)
+    rc = _check(_lib.iga_mass_solve_noalloc(ops, dtype, _dptr(b), _dptr(x), nrhs, rtol, max_it, flags,
+                                            iters, rel, _stream(stream)), ok)
     if want_stats:
         return rc, np.array(iters[:]), np.array(rel[:])
     return rc, None, None
