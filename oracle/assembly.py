@@ -83,6 +83,30 @@ class Space:
         G = np.take_along_axis(Bd, loc[:, None, :].repeat(self.quad_pts, 1), axis=2)
         return x, w, V, G
 
+    def element_volumes(self, elems):
+        """Ve[e, a] = int_element phi_a det J ds for the (p+1)^dim local functions a
+        (colex local index, as in element_matrices) of elements elems (nE, dim)."""
+        elems = np.asarray(elems, dtype=np.int64).reshape(-1, self.dim)
+        d, p, nq = self.dim, self.p, self.quad_pts
+        tabs = [self._tables_1d(elems[:, k]) for k in range(d)]
+        gidx = [tuple(reversed(g)) for g in itertools.product(range(nq), repeat=d)]
+        aidx = [tuple(reversed(a)) for a in itertools.product(range(p + 1), repeat=d)]
+        nE, NQ, NL = len(elems), len(gidx), len(aidx)
+        s = np.empty((nE, NQ, d))
+        w = np.ones((nE, NQ))
+        for qi, g in enumerate(gidx):
+            for k in range(d):
+                s[:, qi, k] = tabs[k][0][:, g[k]]
+                w[:, qi] *= tabs[k][1][:, g[k]]
+        _, J = self.geometry(s)
+        detJ = np.linalg.det(J)
+        val = np.ones((nE, NQ, NL))
+        for qi, g in enumerate(gidx):
+            for ai, a in enumerate(aidx):
+                for k in range(d):
+                    val[:, qi, ai] *= tabs[k][2][:, g[k], a[k]]
+        return np.einsum('eqa,eq->ea', val, w * detJ)
+
     def element_matrices(self, elems):
         """Element stiffness and mass matrices for element multi-indices elems (nE, dim).
 
@@ -185,3 +209,21 @@ def stencil_to_csr(space, T, rows=None):
     A = sp.csr_matrix((np.concatenate(vv), (np.concatenate(ii), np.concatenate(jj))),
                       shape=(space.N, space.N))
     return A
+
+
+def lumped_mass(space, rows):
+    """D_ii = integral over Omega of B_i = int_{[0,1]^d} phi_i det J ds (Sec. 3.4,
+    remark on volume preservation), by the element Gauss rule of the space summed
+    over the elements of supp(phi_i).  rows: (R, dim) multi-indices; returns (R,).
+    """
+    rows = np.asarray(rows, dtype=np.int64).reshape(-1, space.dim)
+    d, p, ne = space.dim, space.p, space.n_el
+    loc = np.array([tuple(reversed(a)) for a in itertools.product(range(p + 1), repeat=d)],
+                   dtype=np.int64)
+    out = np.zeros(len(rows))
+    for ai, a in enumerate(loc):
+        e = rows - a[None, :]                          # element whose local function a is phi_i
+        ok = np.all((e >= 0) & (e < ne), axis=1)
+        if ok.any():
+            out[ok] += space.element_volumes(e[ok])[:, ai]
+    return out

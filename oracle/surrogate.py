@@ -22,7 +22,7 @@ Steps, in the paper's order:
 """
 import numpy as np
 
-from .assembly import true_rows
+from .assembly import lumped_mass, true_rows
 from .bspline import collocation
 
 
@@ -142,6 +142,23 @@ class Surrogate:
         off = np.ones(sp.D, dtype=bool)
         off[t0] = False
         SK[:, t0] = -SK[:, off].sum(axis=1)
+        return SK, SM
+
+    def rows_volume_preserving(self, rows):
+        """Surrogate rows with the volume-preserving mass (Sec. 3.4, remark on
+        volume preservation): M~ = D + M~_0, D_ii = integral of B_i, and M~_0 built
+        like K~ (Eq. DefinitionOfSurrogateMatrixSymmetricKernel) from the mass
+        stencil functions: the off-diagonal entries are those of M~ and the
+        diagonal of M~_0 is minus its off-diagonal row sum.  Hence
+        [M~]_ii = D_ii - sum_{j != i} [M~]_ij and sum_ij [M~]_ij = |Omega|.
+        Returns SK, SM (SK as in rows())."""
+        sp = self.space
+        rows = np.asarray(rows, dtype=np.int64).reshape(-1, sp.dim)
+        SK, SM = self.rows(rows)
+        t0 = (sp.D - 1) // 2
+        off = np.ones(sp.D, dtype=bool)
+        off[t0] = False
+        SM[:, t0] = lumped_mass(sp, rows) - SM[:, off].sum(axis=1)
         return SK, SM
 
     def sampling_length(self):
