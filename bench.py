@@ -132,9 +132,10 @@ def run_ours(args, rank, world, device):
         return iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"], 0, stream)
 
     ops = assemble()
+    sflags = iga.IGA_SOLVE_GRAPH if args.solve == "graph" else 0
     wave = iga.iga_wave_create(ops, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
                                f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
-                               cg_max_it=args.cg_max_it, cfl_check=2)
+                               cg_max_it=args.cg_max_it, cfl_check=2, solve_flags=sflags)
     iga.iga_wave_set_timing(wave, True)
 
     def one_pass(old_ops):
@@ -179,6 +180,10 @@ def run_ours(args, rank, world, device):
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     launches = iga.iga_launch_count() - launches0
+    if args.solve == "graph":
+        # the library counts one launch per solve graph; it runs init 1, init 2, zero-RHS,
+        # finish and two kernels per iteration
+        launches += 3 * cg_solves + 2 * cg_it
     ms = ev0.elapsed_time(ev1)
     if world > 1:
         t = torch.tensor([ms], device=device)
@@ -216,12 +221,16 @@ def run_ours(args, rank, world, device):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "dim": w["dim"], "p": w["p"], "n_el": w["n_el"], "N": N,
                    "q": w["q"], "M": w["M"], "nsteps": nsteps, "nshot": args.nshot, "cg_rtol": args.cg_rtol,
+                   "cg_schedule": args.solve,
                    "precision": "FP32 fields/vectors/apply, FP64 quadrature, residual and dot products",
                    "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (
                        (oinfo.nK + oinfo.nM) * oinfo.pitch * 12 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "components": comps,
-        "roofline": {"bound": "hbm", "kernel": "pcg_persistent_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm",
+                     "kernel": ("pcg graph (cgg_phase1_kernel + cgg_phase2_kernel)" if args.solve == "graph"
+                                else "pcg_persistent_kernel"),
+                     "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "bytes_per_row_per_iteration": it_b, "launches": cg_solves,
@@ -293,7 +302,8 @@ def run_e2e(args, ctx):
         o = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
         wv = iga.iga_wave_create(o, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
                                  f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
-                                 cg_max_it=args.cg_max_it)
+                                 cg_max_it=args.cg_max_it,
+                                 solve_flags=iga.IGA_SOLVE_GRAPH if args.solve == "graph" else 0)
         iga.iga_wave_step(wv, nsteps)
         tr = iga.iga_wave_traces(wv, args.nshot, len(rec), nsteps)   # device -> host
         N = iga.iga_ops_info_get(o).N
@@ -342,13 +352,13 @@ def run_batched(args):
         for g in range(2):
             waves.append(iga.iga_wave_create(ops, 8, iga.IGA_F32, W.dt_of(w), src_pos=src[8 * g:8 * g + 8],
                                              f0=10.0, t0=0.1, rec_pos=np.array([[0.5, 0.5]]), nsteps_max=nsteps + 64,
-                                             cg_rtol=args.cg_rtol, cg_max_it=args.cg_max_it, cfl_check=2))
+                                             cg_rtol=args.batched_rtol, cg_max_it=args.cg_max_it, cfl_check=2))
     b = iga.iga_batch_create(waves)
     iga.iga_batch_tune(b, trial_steps=5, rounds=3)
     part = iga.iga_batch_partition(b, len(waves))
     for wv, k in zip(waves, range(len(waves))):
         iga.iga_wave_reset(wv, meshes[k // 2][2])
-    iga.iga_batch_step(b, nsteps, use_graph=True)      # capture + warm-up
+    iga.iga_batch_step(b, min(nsteps, 50), use_graph=True)      # warm-up (a shorter captured launch)
     for wv, k in zip(waves, range(len(waves))):
         iga.iga_wave_reset(wv, meshes[k // 2][2])
     torch.cuda.synchronize()
@@ -405,6 +415,72 @@ def run_batched(args):
             "batched_over_plain": batched / plain,
             "batched_fp32_vs_fp64_rel_l2_error_max": max(errs),
             "batched_partition_blocks": part}
+
+
+def run_adjoint(args):
+    """Gradient of the receiver misfit on the adjoint workload, timed, with its
+    central-difference check.
+
+    3-D p=2, 64^3 elements, sine-perturbed cube (0.1), wave speed on 12^3 cubic
+    B-spline coefficients (seeded smooth perturbation of 1), q=2, M=6, dt = 0.1 h,
+    8 Ricker shots at seeded positions in [0.2, 0.8]^3, 32 receivers per face
+    (192), `adjoint_steps` FP64 leapfrog steps with checkpoints every 50, CG rtol
+    1e-13.  Observed traces come from a second coefficient field through the same
+    forward path.  Timed: J and its gradient through the torch.autograd.Function
+    (assembly, forward with checkpoints, reverse sweep with recomputation).
+    Check: central difference with eps = 1e-6 along one seeded direction against
+    <grad, v>.
+    """
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300.autograd import misfit
+    n_el, nsteps, nshot = 64, args.adjoint_steps, 8
+    dt = 0.1 / n_el
+    theta = inputs.theta_smooth(n=12, dim=3)
+    theta_obs = inputs.theta_smooth(n=12, dim=3, seed=inputs.SEED_THETA_OBS)
+    src = inputs.shot_positions(nshot, dim=3, lo=0.2, hi=0.8, seed=inputs.SEED_SHOTS_3D)
+    rec = inputs.face_receivers(per_face=32)
+    sp = iga.iga_space_create(3, 2, n_el, iga.IGA_MAP_CUBE_SINE, 0.1, iga.IGA_COEF_BSPLINE, 0.0,
+                              theta=inputs.colex(theta_obs), n_theta=12, theta_degree=3)
+    ops = iga.iga_surrogate_assemble(sp, 2, 2, 6)
+    wv = iga.iga_wave_create(ops, nshot, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1, rec_pos=rec,
+                             nsteps_max=nsteps, cg_rtol=1e-13, cg_max_it=5000, cfl_check=1)
+    iga.iga_wave_step(wv, nsteps)
+    obs = iga.iga_wave_traces(wv, nshot, len(rec), nsteps)
+    st = iga.iga_wave_stats_get(wv)
+    lam_min, lam_max = st.lambda_min, st.lambda_max
+    iga.iga_wave_destroy(wv)
+    iga.iga_ops_destroy(ops)
+    iga.iga_space_destroy(sp)
+    problem = dict(dim=3, p=2, n_el=n_el, map_kind=iga.IGA_MAP_CUBE_SINE, map_param=0.1, q=2, M=6, dt=dt,
+                   nsteps=nsteps, checkpoint_every=50, src_pos=src, rec_pos=rec, obs=obs, f0=10.0, t0=0.1,
+                   cg_rtol=1e-13)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    J = misfit(th, problem)
+    J.backward()
+    J = J.detach()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t
+    g = th.grad.numpy().copy()
+    v = np.random.default_rng(41).standard_normal(theta.shape)
+    eps = 1e-6
+    with torch.no_grad():
+        Jp = float(misfit(torch.tensor(theta + eps * v), problem))
+        Jm = float(misfit(torch.tensor(theta - eps * v), problem))
+    fd = (Jp - Jm) / (2 * eps)
+    gv = float(np.sum(g * v))
+    return {"adjoint_workload": ("cube 64^3 p=2, 12^3 theta, 8 shots x %d FP64 steps, checkpoints every 50, "
+                                 "192 receivers" % nsteps),
+            "adjoint_gradient_s": t_grad, "adjoint_shot_steps_per_s": nshot * nsteps / t_grad,
+            "adjoint_J": float(J), "adjoint_grad_dot_v": gv, "adjoint_central_fd": fd,
+            "adjoint_fd_rel_error": abs(gv - fd) / max(abs(gv), 1e-300),
+            "adjoint_dt_sqrt_lambda_max": dt * float(np.sqrt(max(lam_max, 0.0))),
+            "adjoint_lambda_min": lam_min}
 
 
 # ------------------------------------------------------------------ oracle legs
@@ -520,6 +596,8 @@ def main():
     ap.add_argument("--nshot", type=int, default=1)
     ap.add_argument("--cg-rtol", type=float, default=1e-6)
     ap.add_argument("--cg-max-it", type=int, default=2000)
+    ap.add_argument("--solve", default="persistent", choices=["persistent", "graph"],
+                    help="CG schedule of the FP32 waves")
     ap.add_argument("--compare-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--oracle-rows", type=int, default=96)
@@ -527,8 +605,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-mesh leg")
-    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--batched-steps", type=int, default=1000)
+    ap.add_argument("--batched-rtol", type=float, default=3e-7,
+                    help="CG tolerance of the batched FP32 shots (the CG term of the FP32 error is about 15 rtol after 1000 steps)")
     ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="also run the adjoint-gradient leg (several minutes: FP64 forward / reverse sweeps)")
+    ap.add_argument("--adjoint-steps", type=int, default=600)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -554,6 +637,8 @@ def main():
             out["e2e"] = run_e2e(args, ctx)
         if not args.no_batched:
             out["components"].update(run_batched(args))
+        if args.adjoint:
+            out["components"].update(run_adjoint(args))
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(args)
     if world > 1:

@@ -75,10 +75,21 @@ extern "C" {
 /* surrogate_assemble flags */
 #define IGA_TRUE_ONLY     1u  /* full quadrature of every entry: the true K, M (no surrogate) */
 #define IGA_KEEP_SAMPLES  2u  /* keep sample tables and interpolation coefficients for export */
+#define IGA_MASS_VOLUME_PRESERVING 4u
+/* volume-preserving surrogate mass (Sec. 3.4, remark on volume preservation):
+   M~ = D + M~_0, D_ii = int_Omega B_i (Gauss quadrature of phi_i det J), M~_0
+   built like K~ from the mass stencil functions.  The off-diagonal entries are
+   those of the plain M~; the stored diagonal becomes D_ii - sum_{j!=i} M~_ij,
+   so sum_ij M~_ij = |Omega| (up to quadrature of det J).  Every consumer of the
+   M~ fields (apply, mass_solve, waves, adjoint) uses it unchanged. */
 
 /* mass_solve flags */
 #define IGA_SOLVE_PLAIN   1u  /* non-persistent schedule: one launch per CG phase, host-side
                                  convergence test every iteration (reference schedule) */
+#define IGA_SOLVE_GRAPH   2u  /* graph schedule: the phases as full-occupancy launches in one CUDA
+                                 graph whose conditional WHILE node iterates until the device decides
+                                 convergence (no grid barrier, no host round trip); falls back to
+                                 the persistent schedule when the stream is being captured */
 
 /* wave initial conditions */
 #define IGA_INIT_ZERO         0
@@ -137,6 +148,15 @@ int iga_space_info_get(const iga_space* space, iga_space_info* out);
  * Builds FP64 fields and FP32 copies, and the inverse Jacobi diagonal of M~.
  * Asynchronous on `stream` except for a final status check (synchronises).
  */
+/* Mesh-dependent sampling length (Sec. 5.2, Eq. MeshDependentSamplingLength):
+ * M(h) = max{1, floor(C h^(eps - 1 + (p+a)/(q+b)))}, evaluated in FP64 on the
+ * host, saturating at INT_MAX.  With q + b > p + a and eps small the sampling
+ * distance H = M h shrinks more slowly than h, so H^(q+b) = o(h^(p+a)).
+ * Needs h > 0, q + b > 0, C > 0, eps > 0, p >= 1 (else IGA_ERR_ARG).
+ * Synchronous, no device work. */
+int iga_sampling_length_for_mesh(double h, int p, int q, double a, double b, double C, double eps,
+                                 int* M_out);
+
 int iga_surrogate_assemble(iga_space* space, int p, int q, int M, unsigned flags,
                            void* stream, iga_ops** out);
 int iga_ops_destroy(iga_ops* ops);

@@ -51,6 +51,14 @@ def sample_indices(m, p, M):
     return lo + offs
 
 
+def mesh_dependent_sampling_length(h, p, q, a=0.0, b=0.0, C=1.0, eps=0.1):
+    """Sampling length M(h) of Eq. MeshDependentSamplingLength (Sec. 5.2):
+    M(h) = max{1, floor(C h^(eps - 1 + (p + a)/(q + b)))}, in FP64."""
+    if not (h > 0 and q + b > 0 and C > 0 and eps > 0):
+        raise ValueError("need h > 0, q + b > 0, C > 0, eps > 0")
+    return max(1, int(np.floor(C * h ** (eps - 1.0 + (p + a) / (q + b)))))
+
+
 def interp_knots(xs, q):
     """Knot vector of order q+1 for interpolation at abscissae xs (de Boor averaging)."""
     xs = np.asarray(xs, dtype=np.float64)

@@ -24,6 +24,7 @@
 
 #include "geom.cuh"
 #include "quad.cuh"
+#include "stencil.cuh"
 #include "host_bspline.h"
 #include "iga_internal.cuh"
 
@@ -264,6 +265,95 @@ __global__ void eval_kernel(const double* __restrict__ coef, int ns, const int* 
     }
 }
 
+// ---------------------------------------------------------------- volume-preserving mass
+// Sec. 3.4 (remark on volume preservation): M~ = D + M~_0 with D_ii = int phi_i
+// det J and M~_0 built like K~ from the mass stencil functions, i.e. the
+// off-diagonal entries of M~ are kept and the diagonal becomes
+// D_ii - sum_{j != i} [M~]_ij.
+//
+// lumped_elem_kernel: per element, the integrals of its (p+1)^d local functions,
+// ve[a][e] (one thread per element, Gauss points in colex order).
+template <int DIM, int P>
+__global__ void lumped_elem_kernel(GeomParams gp, double* __restrict__ ve, int nE, int* status) {
+    constexpr int NL = DIM == 2 ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
+    const int nq = gp.nq;
+    int nqd = nq;
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) nqd *= nq;
+    for (int el = blockIdx.x * blockDim.x + threadIdx.x; el < nE; el += gridDim.x * blockDim.x) {
+        int e[3] = {0, 0, 0};
+        decode<DIM>(el, gp.n_el, e);
+        double acc[NL];
+#pragma unroll
+        for (int a = 0; a < NL; ++a) acc[a] = 0.0;
+        for (int q = 0; q < nqd; ++q) {
+            int g[3] = {0, 0, 0};
+            decode<DIM>(q, nq, g);
+            const double wm = qp_volume(gp, e, g);
+            if (!(wm > 0.0)) atomicOr(status, 2);
+            double b[DIM][P + 1];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+#pragma unroll
+                for (int a = 0; a <= P; ++a) b[k][a] = gp.bval[(e[k] * nq + g[k]) * (P + 1) + a];
+#pragma unroll
+            for (int a = 0; a < NL; ++a) {
+                int al[3] = {0, 0, 0};
+                decode<DIM>(a, P + 1, al);
+                double v = wm;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) v *= b[k][al[k]];
+                acc[a] += v;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NL; ++a) ve[(size_t)a * nE + el] = acc[a];
+    }
+}
+
+// vp_diag_kernel: D_i = sum over the elements of supp(phi_i) (local index a,
+// colex, fixed order) of ve[a][i - a]; then field 0 of M~ = D_i minus the
+// off-diagonal row sum sum_u F_u[i] + F_u[i - Delta_u] (entries leaving the grid
+// are stored as 0).
+template <int DIM, int P>
+__global__ void vp_diag_kernel(const double* __restrict__ ve, int n_el, int m, long long N, double* fM,
+                               long long pitch) {
+    constexpr int NL = DIM == 2 ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
+    constexpr int NF = StencilShape<DIM, P>::T0;
+    long long nE = n_el;
+    for (int k = 1; k < DIM; ++k) nE *= n_el;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        int ii[3] = {0, 0, 0};
+        long long r = i;
+        for (int k = 0; k < DIM; ++k) {
+            ii[k] = (int)(r % m);
+            r /= m;
+        }
+        double d = 0.0;
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+            int al[3] = {0, 0, 0};
+            decode<DIM>(a, P + 1, al);
+            bool ok = true;
+            long long el = 0;
+            for (int k = DIM - 1; k >= 0; --k) {
+                const int ek = ii[k] - al[k];
+                ok = ok && ek >= 0 && ek < n_el;
+                el = el * n_el + ek;
+            }
+            if (ok) d += ve[(size_t)a * nE + el];
+        }
+        double off = 0.0;
+        for (int u = 0; u < NF; ++u) {
+            const long long dl = field_delta<DIM, P>(u, m);
+            const double* F = fM + (size_t)(u + 1) * pitch;
+            off += F[i];
+            if (i - dl >= 0) off += F[i - dl];
+        }
+        fM[i] = d - off;
+    }
+}
+
 // ---------------------------------------------------------------- finalize
 __global__ void finalize_kernel(const double* __restrict__ fK, const double* __restrict__ fM, float* fK32,
                                 float* fM32, double* dinv64, float* dinv32, int nK, int nM, long long N,
@@ -320,6 +410,26 @@ static int launch_samples(const iga_space* s, const int* d_samp, iga_ops* ops, c
     sample_rows_kernel<DIM, P><<<nsd, 64, smem, st>>>(s->gp, d_samp, ops->ns, ops->sK.as<double>(),
                                                        ops->sM.as<double>(), ops->status.as<int>());
     IGA_LAUNCH_CHECK("sample_rows_kernel");
+    return IGA_OK;
+}
+
+template <int DIM, int P>
+static int launch_volume_preserving(const iga_space* s, iga_ops* ops, cudaStream_t st) {
+    constexpr int NL = DIM == 2 ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
+    long long nE = 1;
+    for (int k = 0; k < DIM; ++k) nE *= s->n_el;
+    DevBuf ve;
+    int rc = ve.alloc(sizeof(double) * NL * nE);
+    if (rc) return rc;
+    const int ge = (int)std::min<long long>((nE + 127) / 128, 152 * 32);
+    lumped_elem_kernel<DIM, P><<<ge, 128, 0, st>>>(s->gp, ve.as<double>(), (int)nE, ops->status.as<int>());
+    IGA_LAUNCH_CHECK("lumped_elem_kernel");
+    const int gr = (int)std::min<long long>((ops->N + 255) / 256, 152 * 16);
+    vp_diag_kernel<DIM, P><<<gr, 256, 0, st>>>(ve.as<double>(), s->n_el, s->m, ops->N, ops->fM64.as<double>(),
+                                               ops->pitch);
+    IGA_LAUNCH_CHECK("vp_diag_kernel");
+    // ve is released when this returns: wait for the kernels that read it
+    IGA_CUDA(cudaStreamSynchronize(st));
     return IGA_OK;
 }
 
@@ -538,6 +648,16 @@ extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigne
         cudaEventRecord(tm.ev[2], st);
         cudaEventRecord(tm.ev[3], st);
     }
+    if (flags & IGA_MASS_VOLUME_PRESERVING) {
+        const int d2 = dim * 10 + p;
+        rc = d2 == 21   ? launch_volume_preserving<2, 1>(s, ops, st)
+             : d2 == 22 ? launch_volume_preserving<2, 2>(s, ops, st)
+             : d2 == 23 ? launch_volume_preserving<2, 3>(s, ops, st)
+             : d2 == 31 ? launch_volume_preserving<3, 1>(s, ops, st)
+             : d2 == 32 ? launch_volume_preserving<3, 2>(s, ops, st)
+                        : fail(IGA_ERR_ARG, "unsupported (dim, p) for the volume-preserving mass");
+        if (rc) return bail(rc);
+    }
     cudaEventRecord(tm.ev[4], st);
     {
         const long long total = (long long)(ops->nK + ops->nM) * pitch;
@@ -573,6 +693,17 @@ extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigne
         ops->cM.release();
     }
     *out = ops;
+    return IGA_OK;
+}
+
+extern "C" int iga_sampling_length_for_mesh(double h, int p, int q, double a, double b, double C, double eps,
+                                            int* M_out) {
+    if (!M_out) return fail(IGA_ERR_ARG, "null argument");
+    if (!(h > 0.0) || !(q + b > 0.0) || !(C > 0.0) || !(eps > 0.0) || p < 1)
+        return fail(IGA_ERR_ARG, "need h > 0, q + b > 0, C > 0, eps > 0, p >= 1");
+    // Eq. MeshDependentSamplingLength, FP64; saturates at INT_MAX
+    const double v = std::floor(C * std::pow(h, eps - 1.0 + (p + a) / (q + b)));
+    *M_out = v >= 2147483647.0 ? 2147483647 : std::max(1, (int)v);
     return IGA_OK;
 }
 

@@ -21,6 +21,7 @@
 
 #include "cg.cuh"
 #include "iga_internal.cuh"
+#include "leapfrog.cuh"
 #include "stencil.cuh"
 
 namespace iga {
@@ -38,6 +39,7 @@ struct BatchProb {
     long long pitch;
     int N, m;
     float* U[2];        // u^n in U[n % 2]
+    float* L[2];        // low parts of the compensated state, alongside U
     float* a;           // CG solution / next initial guess
     float* b;           // right-hand side
     double* r;          // CG residual (FP64)
@@ -96,6 +98,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         const int n = n0 + s;
         const float* cur = q.U[n & 1];
         float* nxt = q.U[(n + 1) & 1];   // holds u^{n-1}; receives u^{n+1}
+        const float* curlo = q.L[n & 1];
+        float* nxtlo = q.L[(n + 1) & 1];
         // ---- force + source
         {
             const float amp = (float)(q.amp * ricker_dev(n * q.dt, q.f0, q.t0));
@@ -243,7 +247,11 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const long long o = (long long)r * q.ld + i;
-                    nxt[o] = (n == 0) ? cur[o] + 0.5f * dt2 * q.a[o] : 2.f * cur[o] - nxt[o] + dt2 * q.a[o];
+                    float hn, ln;
+                    leapfrog_comp(cur[o], curlo[o], nxt[o], nxtlo[o], __fmul_rn(n == 0 ? 0.5f * dt2 : dt2, q.a[o]),
+                                  n == 0, hn, ln);
+                    nxt[o] = hn;
+                    nxtlo[o] = ln;
                 }
             }
         }
@@ -253,8 +261,10 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
             for (int k = threadIdx.x; k < R * q.nrec; k += blockDim.x) {
                 const int r = k / q.nrec, rec = k % q.nrec;
                 double acc = 0.0;
-                for (int l = 0; l < q.nloc; ++l)
-                    acc += q.rec_w[rec * q.nloc + l] * (double)nxt[(long long)r * q.ld + q.rec_idx[rec * q.nloc + l]];
+                for (int l = 0; l < q.nloc; ++l) {
+                    const long long o = (long long)r * q.ld + q.rec_idx[rec * q.nloc + l];
+                    acc += q.rec_w[rec * q.nloc + l] * ((double)nxt[o] + (double)nxtlo[o]);
+                }
                 q.traces[((size_t)r * q.nrec + rec) * q.nsteps_max + n] = acc;
             }
         }
@@ -367,9 +377,12 @@ static int batch_sync(iga_batch* b, cudaStream_t st) {
     for (int k = 0; k < b->nprob; ++k) {
         iga_wave* w = b->waves[k];
         BatchProb& q = b->hp[k];
-        if (q.U[w->step & 1] != w->u.ptr || q.U[(w->step + 1) & 1] != w->uprev.ptr) {
+        if (q.U[w->step & 1] != w->u.ptr || q.U[(w->step + 1) & 1] != w->uprev.ptr ||
+            q.L[w->step & 1] != w->ulo.ptr || q.L[(w->step + 1) & 1] != w->uprevlo.ptr) {
             q.U[w->step & 1] = w->u.as<float>();
             q.U[(w->step + 1) & 1] = w->uprev.as<float>();
+            q.L[w->step & 1] = w->ulo.as<float>();
+            q.L[(w->step + 1) & 1] = w->uprevlo.as<float>();
             dirty = true;
         }
         IGA_CUDA(cudaMemcpyAsync(q.step, &w->step, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -460,6 +473,8 @@ extern "C" int iga_batch_create(int nprob, iga_wave* const* waves, iga_batch** o
         // u^n of the wave is in U[n % 2]
         q.U[w->step & 1] = w->u.as<float>();
         q.U[(w->step + 1) & 1] = w->uprev.as<float>();
+        q.L[w->step & 1] = w->ulo.as<float>();
+        q.L[(w->step + 1) & 1] = w->uprevlo.as<float>();
         q.a = w->a.as<float>();
         q.b = w->b.as<float>();
         q.r = (double*)take(8 * v);
@@ -562,6 +577,8 @@ extern "C" int iga_batch_step(iga_batch* b, int nsteps, int use_graph, void* str
         const BatchProb& q = b->hp[k];
         w->u.ptr = q.U[w->step & 1];
         w->uprev.ptr = q.U[(w->step + 1) & 1];
+        w->ulo.ptr = q.L[w->step & 1];
+        w->uprevlo.ptr = q.L[(w->step + 1) & 1];
     }
     const int errw = (int)cnt[0];
     if (errw & 4) return fail(IGA_ERR_TIMEOUT, "partition barrier timed out in batch");
@@ -588,6 +605,8 @@ extern "C" int iga_batch_tune(iga_batch* b, int trial_steps, int rounds, void* s
         for (int k = 0; k < b->nprob; ++k) {
             b->waves[k]->u.ptr = b->hp[k].U[b->waves[k]->step & 1];
             b->waves[k]->uprev.ptr = b->hp[k].U[(b->waves[k]->step + 1) & 1];
+            b->waves[k]->ulo.ptr = b->hp[k].L[b->waves[k]->step & 1];
+            b->waves[k]->uprevlo.ptr = b->hp[k].L[(b->waves[k]->step + 1) & 1];
         }
         double mean = 0.0;
         std::vector<double> t(b->nprob);

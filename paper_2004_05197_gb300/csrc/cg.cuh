@@ -89,14 +89,34 @@ struct PlainLoadB {
     __device__ __forceinline__ T operator()(int r, int idx) const { return x[r * xs + idx]; }
 };
 
+// One lane's share of a fixed-order sum over blocks: partials[b * stride + idx]
+// for b = lane, lane + 32, ... in increasing b.  The loads of eight consecutive
+// terms are issued before they are added (same order, so the same result), so a
+// long sum waits for L2 latency once per eight terms instead of once per term.
+__device__ __forceinline__ double lane_partial_sum(const double* partials, int nblocks, int stride, int idx,
+                                                   int lane) {
+    double s = 0.0;
+    for (int b0 = lane; b0 < nblocks; b0 += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int b = b0 + 32 * j;
+            v[j] = b < nblocks ? __ldcg(partials + (size_t)b * stride + idx) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (b0 + 32 * j < nblocks) s += v[j];
+    }
+    return s;
+}
+
 // Sum over the blocks of a partition of partials[b * stride + off + k] (k < K)
 // into out[k] (shared); fixed order, so every block gets the identical value.
 template <int K>
 __device__ __forceinline__ void grid_sum_b(const double* partials, int nblocks, int stride, int off, double* out) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = w; k < K; k += nw) {
-        double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32) s += __ldcg(partials + (size_t)b * stride + off + k);
+        double s = lane_partial_sum(partials, nblocks, stride, off + k, lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) out[k] = s;

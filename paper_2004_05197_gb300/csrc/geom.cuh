@@ -118,6 +118,26 @@ __device__ inline double coef_c(const GeomParams& gp, const int* e, const int* g
 
 // Pulled-back weights at Gauss point (e, g): G (packed symmetric) and wm.
 // Returns det J (callers flag det J <= 0).
+// Volume weight w det J at Gauss point g of element e (integrands without
+// derivatives, e.g. the lumped mass).
+__device__ inline double qp_volume(const GeomParams& gp, const int* e, const int* g) {
+    const int d = gp.dim;
+    double s[3] = {0, 0, 0}, x[3] = {0, 0, 0}, J[3][3];
+    double w = 1.0;
+    for (int k = 0; k < d; ++k) {
+        s[k] = gp.qs[e[k] * gp.nq + g[k]];
+        w *= gp.qw[g[k]];
+    }
+    map_eval(gp, s, x, J);
+    double det;
+    if (d == 2)
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    else
+        det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    return w * det;
+}
+
 __device__ inline double qp_weights(const GeomParams& gp, const int* e, const int* g, double* G,
                                     double& wm) {
     const int d = gp.dim;

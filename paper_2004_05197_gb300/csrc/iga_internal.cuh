@@ -99,6 +99,7 @@ struct iga_wave {
     int dtype, nshot, nrec, nloc, step;
     long long N;
     iga::DevBuf u, uprev, a, b, traces, src_idx, src_w, rec_idx, rec_w, work, counters;
+    iga::DevBuf ulo, uprevlo;        // FP32 waves: low parts of the compensated state (hi + lo)
     iga::DevBuf greville, centres;   // pulse initial condition inputs (GAUSS_PULSE)
     int timing = 0;
     long long cg_solves = 0;

@@ -1,25 +1,20 @@
-// Jacobi-PCG on the surrogate mass M~ (mass_solve) and leapfrog time stepping
-// (wave_*).
+// Jacobi-PCG on the surrogate mass M~ (mass_solve).
 //
-// PCG recurrence (standard preconditioned CG, diagonal preconditioner D^-1):
-//   r = b - M~x, z = D^-1 r, p = z, rz = (r, z)
-//   repeat while ||r|| > rtol ||b|| and it < max_it:
-//     q = M~p, alpha = rz / (p, q), x += alpha p, r -= alpha q, z = D^-1 r,
-//     beta = (r, z)_new / rz, p = z + beta p
-// The update p = z + beta p is folded into the next mass apply: the apply reads
-// z and the previous p at the neighbours and forms z + beta p on the fly, while
-// the row's own new p is written to the other half of a double buffer.  One
-// iteration is thus two grid-wide phases:
-//   A: p_new = z + beta p_old, q = M~ p_new, partial (p_new, q)
-//   B: x += alpha p_new, r -= alpha q, z = D^-1 r, partial (r, z), (r, r)
-// FP32 dtype: fields, x, z, p, q in FP32; the residual r and every dot product
-// in FP64.  Dot products are reduced deterministically: per-block partials,
-// then a fixed-order warp reduction that every block performs identically.
+// Preconditioned CG with the diagonal (Jacobi) preconditioner D^-1 of M~, in
+// the Chronopoulos-Gear arrangement (recurrence below, at the CG phases): one
+// mass apply of a single gathered vector and one joint reduction per iteration,
+// the same iterates as the textbook recurrence in exact arithmetic.  Each
+// iteration is two grid-wide phases: a vector update (phase 1) and the mass
+// apply with its dot product (phase 2).
+// FP32 dtype: fields and the vectors u, w, p, s, x in FP32; the residual r and
+// every dot product in FP64.  Dot products are reduced deterministically:
+// per-block partials, then a fixed-order warp reduction that every block
+// performs identically.
 //
 // Default schedule: one cooperative (persistent) launch runs all iterations,
 // phases separated by a bounded grid barrier; convergence is decided on the
 // device.  IGA_SOLVE_PLAIN: the same phases as separate launches with the
-// scalars read back to the host every phase (the plain reference schedule).
+// scalars read back to the host every iteration (the plain reference schedule).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -71,18 +66,6 @@ struct PlainLoad {
         return IGA_IN(o, ext, 1) ? x[o] : T(0);
     }
 };
-template <typename T, int R>
-struct CombLoad {   // z + beta p_old, formed on the fly
-    const T* z;
-    const T* p;
-    long long xs;
-    long long ext;
-    T beta[R];
-    __device__ __forceinline__ T operator()(int r, int idx) const {
-        const long long o = r * xs + idx;
-        return IGA_IN(o, ext, 2) ? fma(beta[r], p[o], z[o]) : T(0);
-    }
-};
 
 // Sum over blocks of partials[b * stride + off + k] (k < K) into out[k]
 // (shared), fixed order; every block computes the identical result.
@@ -90,11 +73,9 @@ template <int K>
 __device__ __forceinline__ void grid_sum(const double* partials, int nblocks, int stride, int off, double* out) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = w; k < K; k += kCgWarps) {
-        double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32)
-            s += IGA_IN((long long)b * stride + off + k, (long long)nblocks * stride, 14)
-                     ? __ldcg(partials + (size_t)b * stride + off + k)
-                     : 0.0;
+        double s = IGA_IN((long long)(nblocks - 1) * stride + off + k, (long long)nblocks * stride, 14)
+                       ? lane_partial_sum(partials, nblocks, stride, off + k, lane)
+                       : 0.0;
 #pragma unroll
         for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, off2);
         if (lane == 0) out[k] = s;
@@ -373,8 +354,7 @@ template <int K>
 __global__ void grid_sum_kernel(const double* partials, int nblocks, int stride, int off, double* out) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = w; k < K; k += kCgWarps) {
-        double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * stride + off + k];
+        double s = lane_partial_sum(partials, nblocks, stride, off + k, lane);
 #pragma unroll
         for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_down_sync(0xffffffffu, s, off2);
         if (lane == 0) out[k] = s;
@@ -395,6 +375,7 @@ struct CgWork {
     double* relres;
     double* sc;   // plain schedule scalars [3R]
     double* red;  // plain schedule reduced values [3R]
+    void* gs;     // graph schedule scalar state (CgGState, <= 256 bytes)
 };
 
 template <typename T>
@@ -418,6 +399,7 @@ static CgWork carve(void* base, long long N /* leading dimension of the internal
     w.relres = (double*)take(sizeof(double) * R);
     w.sc = (double*)take(sizeof(double) * 3 * R);
     w.red = (double*)take(sizeof(double) * 3 * R);
+    w.gs = take(256);
     return w;
 }
 
@@ -425,7 +407,213 @@ static size_t carve_bytes(size_t es, long long N, int R, int nblocks) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     return up(sizeof(double) * (size_t)R * N) + 4 * up(es * (size_t)R * N) +
            up(sizeof(double) * (size_t)nblocks * 10 * R) + 2 * up(64) + up(sizeof(int) * R) +
-           3 * up(sizeof(double) * 3 * R) + 256;
+           3 * up(sizeof(double) * 3 * R) + up(256) + 256;
+}
+
+// ---------------------------------------------------------------- graph schedule
+// IGA_SOLVE_GRAPH: the phases as separate full-occupancy launches inside one
+// CUDA graph,
+//   init 1 -> init 2 -> zero x of zero RHS -> WHILE { phase 1 -> phase 2 } -> finish,
+// whose conditional WHILE node repeats the iteration until the device decides
+// convergence.  Every phase-2 launch ends with a ticket counter: the last block
+// to finish sums the per-block partials in fixed order, updates the scalars in
+// CgGState and sets the loop condition.  Kernel boundaries order the phases,
+// so there is neither a grid barrier nor a host round trip per iteration.
+constexpr int kGThreads = 256;
+constexpr int kGWarps = kGThreads / 32;
+
+struct CgGState {
+    double gam[4], rr[4], bnorm[4], alpha[4], beta[4];
+    int active[4], iters[4];
+    int it;
+    unsigned ticket;
+};
+
+template <int DIM, int P, typename T, int R>
+__global__ void __launch_bounds__(kGThreads, (R == 1 ? 8 : 2)) cgg_init1_kernel(CgVecs<T> v, double* partials) {
+    __shared__ double wsum[kGWarps * 3 * R];
+    __shared__ double red[3 * R];
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
+    double part[3 * R];
+    fill_delta_table<DIM, P>(sdl, v.m);
+    cg_init1<DIM, P, T, R>(v, part, sdl);
+    block_sum<3 * R, kGWarps>(part, wsum, red);
+    if (threadIdx.x < 3 * R) partials[(size_t)blockIdx.x * kCgStride<R> + 6 * R + threadIdx.x] = red[threadIdx.x];
+}
+
+template <int DIM, int P, typename T, int R, bool INIT>
+__global__ void __launch_bounds__(kGThreads, (R == 1 ? 8 : 2))
+    cgg_phase2_kernel(CgVecs<T> v, double* partials, CgGState* gs, double rtol, int max_it, int* err,
+                      cudaGraphConditionalHandle loop) {
+    constexpr int S = kCgStride<R>;
+    __shared__ double wsum[kGWarps * R];
+    __shared__ double red[3 * R], red2[R];
+    __shared__ int active[R];
+    __shared__ int sdl[StencilShape<DIM, P>::T0];
+    __shared__ int last;
+    double part[R];
+    if (threadIdx.x < R) active[threadIdx.x] = INIT ? 1 : gs->active[threadIdx.x];
+    fill_delta_table<DIM, P>(sdl, v.m);   // ends with __syncthreads
+    cg_phase2<DIM, P, T, R>(v, active, part, sdl);
+    block_sum<R, kGWarps>(part, wsum, red);
+    if (threadIdx.x < R) partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&gs->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    grid_sum_b<(INIT ? 3 : 2) * R>(partials, gridDim.x, S, INIT ? 6 * R : 0, red);
+    grid_sum_b<R>(partials, gridDim.x, S, 4 * R, red2);
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        if (INIT) {
+            gs->gam[r] = red[3 * r];
+            gs->rr[r] = red[3 * r + 1];
+            gs->bnorm[r] = sqrt(red[3 * r + 2]);
+            gs->beta[r] = 0.0;
+            gs->iters[r] = 0;
+            int act = gs->bnorm[r] > 0.0 && !(rtol > 0.0 && sqrt(gs->rr[r]) <= rtol * gs->bnorm[r]);
+            const double d = red2[r];
+            if (act && (!(d > 0.0) || !isfinite(d))) {
+                act = 0;
+                atomicOr(err, 1);
+            }
+            gs->alpha[r] = act ? gs->gam[r] / d : 0.0;
+            gs->active[r] = act;
+        } else if (gs->active[r]) {
+            int brk = 0, act = 1;
+            cg_scalars(red[2 * r], red[2 * r + 1], red2[r], rtol, gs->bnorm[r], gs->gam[r], gs->alpha[r], gs->beta[r],
+                       act, gs->iters[r], gs->rr[r], &brk);
+            gs->active[r] = act;
+            if (brk) atomicOr(err, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int r = 0; r < R; ++r) any |= gs->active[r];
+        const int it = INIT ? 0 : gs->it + 1;
+        gs->it = it;
+        gs->ticket = 0;
+        cudaGraphSetConditional(loop, (any && it < max_it) ? 1u : 0u);
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kGThreads, (R == 1 ? 8 : 2)) cgg_phase1_kernel(CgVecs<T> v, double* partials,
+                                                                                  const CgGState* gs) {
+    __shared__ double wsum[kGWarps * 2 * R];
+    __shared__ double red[2 * R], alpha[R], beta[R];
+    __shared__ int active[R];
+    if (threadIdx.x < R) {
+        alpha[threadIdx.x] = gs->alpha[threadIdx.x];
+        beta[threadIdx.x] = gs->beta[threadIdx.x];
+        active[threadIdx.x] = gs->active[threadIdx.x];
+    }
+    __syncthreads();
+    double part[2 * R];
+    cg_phase1<T, R>(v, alpha, beta, active, part);
+    block_sum<2 * R, kGWarps>(part, wsum, red);
+    if (threadIdx.x < 2 * R) partials[(size_t)blockIdx.x * kCgStride<R> + threadIdx.x] = red[threadIdx.x];
+}
+
+// a zero right-hand side has the solution 0
+template <typename T, int R>
+__global__ void cgg_zero_kernel(CgVecs<T> v, const CgGState* gs) {
+    for (int r = 0; r < R; ++r)
+        if (!(gs->bnorm[r] > 0.0))
+            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x)
+                v.x[(size_t)r * v.ldu + i] = T(0);
+}
+
+template <int R>
+__global__ void cgg_finish_kernel(const CgGState* gs, double rtol, int* iters_out, double* relres_out,
+                                  long long* iter_acc, int* status_acc) {
+    const int r = threadIdx.x;
+    if (r >= R) return;
+    const double rel = gs->bnorm[r] > 0.0 ? sqrt(gs->rr[r]) / gs->bnorm[r] : 0.0;
+    iters_out[r] = gs->iters[r];
+    relres_out[r] = rel;
+    if (iter_acc) atomicAdd((unsigned long long*)iter_acc, (unsigned long long)gs->iters[r]);
+    if (status_acc && rtol > 0.0 && rel > rtol) atomicOr(status_acc, 8);
+}
+
+// Grid of the graph-schedule phases: two waves of resident blocks, at most one
+// block per 256 rows.
+template <int DIM, int P, typename T, int R>
+static int cgg_blocks(long long N) {
+    static int per = 0, sms = 0;
+    if (!per) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cgg_phase2_kernel<DIM, P, T, R, false>, kGThreads, 0);
+        per = std::max(1, per);
+    }
+    return (int)std::max(1LL, std::min<long long>((N + kGThreads - 1) / kGThreads, 2LL * sms * per));
+}
+
+// Builds, instantiates and launches the graph of one solve chunk.
+template <int DIM, int P, typename T, int R>
+static int cgg_launch(CgVecs<T> v, double* partials, CgGState* gs, int* err, double rtol, int max_it, int grid,
+                      int* iters_out, double* relres_out, long long* iter_acc, int* status_acc, cudaStream_t st) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int rc = IGA_OK;
+    auto check = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && rc == IGA_OK) rc = cuda_fail(e, what);
+        return e == cudaSuccess;
+    };
+    auto kernel_node = [&](cudaGraph_t gr, const void* fn, void** args, const cudaGraphNode_t* dep, size_t ndep,
+                           int blocks, int threads, cudaGraphNode_t* out) {
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void*>(fn);
+        kp.gridDim = dim3(blocks);
+        kp.blockDim = dim3(threads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        return check(cudaGraphAddKernelNode(out, gr, dep, ndep, &kp), "cudaGraphAddKernelNode(cg)");
+    };
+    if (check(cudaGraphCreate(&g, 0), "cudaGraphCreate(cg)")) {
+        cudaGraphConditionalHandle loop;
+        cudaGraphNode_t n_init1, n_init2, n_zero, n_loop, n_finish, n_p1, n_p2;
+        if (check(cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault),
+                  "cudaGraphConditionalHandleCreate(cg)")) {
+            void* a_init1[] = {&v, &partials};
+            void* a_p2[] = {&v, &partials, &gs, &rtol, &max_it, &err, &loop};
+            void* a_zero[] = {&v, &gs};
+            void* a_p1[] = {&v, &partials, &gs};
+            void* a_fin[] = {&gs, &rtol, &iters_out, &relres_out, &iter_acc, &status_acc};
+            bool ok = kernel_node(g, (const void*)cgg_init1_kernel<DIM, P, T, R>, a_init1, nullptr, 0, grid, kGThreads,
+                                  &n_init1) &&
+                      kernel_node(g, (const void*)cgg_phase2_kernel<DIM, P, T, R, true>, a_p2, &n_init1, 1, grid,
+                                  kGThreads, &n_init2) &&
+                      kernel_node(g, (const void*)cgg_zero_kernel<T, R>, a_zero, &n_init2, 1, 152, kGThreads, &n_zero);
+            if (ok) {
+                cudaGraphNodeParams cp = {};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = loop;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                ok = check(cudaGraphAddNode(&n_loop, g, &n_zero, nullptr, 1, &cp), "cudaGraphAddNode(cg loop)");
+                if (ok) {
+                    cudaGraph_t body = cp.conditional.phGraph_out[0];
+                    ok = kernel_node(body, (const void*)cgg_phase1_kernel<T, R>, a_p1, nullptr, 0, grid, kGThreads,
+                                     &n_p1) &&
+                         kernel_node(body, (const void*)cgg_phase2_kernel<DIM, P, T, R, false>, a_p2, &n_p1, 1, grid,
+                                     kGThreads, &n_p2) &&
+                         kernel_node(g, (const void*)cgg_finish_kernel<R>, a_fin, &n_loop, 1, 1, 32, &n_finish);
+                }
+            }
+            if (ok && check(cudaGraphInstantiate(&ge, g, 0), "cudaGraphInstantiate(cg)"))
+                if (check(cudaGraphLaunch(ge, st), "cudaGraphLaunch(cg)")) count_launch();
+        }
+    }
+    if (ge) cudaGraphExecDestroy(ge);   // freed once the launched work completes
+    if (g) cudaGraphDestroy(g);
+    return rc;
 }
 
 template <int DIM, int P, typename T, int R>
@@ -448,8 +636,10 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
     const long long N = ops->N;
     const long long ldw = (N + 3) / 4 * 4;
     const int nblocks = cg_blocks<DIM, P, T, R>();
-    if (carve_bytes(sizeof(T), ldw, R, nblocks) > work_bytes) return fail(IGA_ERR_ARG, "CG workspace too small");
-    CgWork w = carve<T>(work, ldw, R, nblocks);
+    const int ggrid = cgg_blocks<DIM, P, T, R>(N);
+    const int nb_carve = std::max(nblocks, ggrid);
+    if (carve_bytes(sizeof(T), ldw, R, nb_carve) > work_bytes) return fail(IGA_ERR_ARG, "CG workspace too small");
+    CgWork w = carve<T>(work, ldw, R, nb_carve);
     CgVecs<T> v;
     v.F = (sizeof(T) == 8) ? (const T*)ops->fM64.ptr : (const T*)ops->fM32.ptr;
     v.pitch = ops->pitch;
@@ -487,11 +677,24 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
         c.relres_out = w.relres;
         c.iter_acc = iter_acc;
         c.status_acc = status_acc;
-        void* args[] = {&v, &c};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_persistent_kernel<DIM, P, T, R>, nblocks,
-                                                    kCgThreads, args, 0, st);
-        count_launch();
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(pcg)");
+        bool use_graph = (flags & IGA_SOLVE_GRAPH) != 0;
+        if (use_graph) {
+            // a graph launch is not issued into a stream under capture: persistent schedule there
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) use_graph = false;
+        }
+        if (use_graph) {
+            IGA_CUDA(cudaMemsetAsync(w.gs, 0, sizeof(CgGState), st));
+            const int rc = cgg_launch<DIM, P, T, R>(v, w.partials, (CgGState*)w.gs, w.err, rtol, max_it, ggrid,
+                                                   w.iters, w.relres, iter_acc, status_acc, st);
+            if (rc) return rc;
+        } else {
+            void* args[] = {&v, &c};
+            cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_persistent_kernel<DIM, P, T, R>, nblocks,
+                                                        kCgThreads, args, 0, st);
+            count_launch();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(pcg)");
+        }
 #ifdef IGA_BOUNDS_CHECK
         {
             long long rec[4] = {0, 0, 0, 0};
@@ -632,22 +835,25 @@ static int pcg_typed(const iga_ops* ops, const T* b, T* x, long long ldu, int nr
     return IGA_OK;
 }
 
-size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
-    (void)nrhs;
+// Per-block partials are sized for the larger of the persistent grid and the
+// graph-schedule grid (two waves of up to 8 resident 256-thread blocks per SM).
+static int work_blocks() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nb = std::max(1, sms) * kCgMaxBlocksPerSM;
+    return std::max(1, sms) * std::max(kCgMaxBlocksPerSM, 16);
+}
+
+size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
+    (void)nrhs;
+    const int nb = work_blocks();
     return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, 4, nb);   // R = 4 is the largest chunk
 }
 
 // Workspace for exactly the chunks pcg_typed runs for nrhs right-hand sides
 // (4-wide chunks while at least 4 remain, then single ones).
 size_t mass_solve_work_bytes_nrhs(const iga_ops* ops, int dtype, int nrhs) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nb = std::max(1, sms) * kCgMaxBlocksPerSM;
+    const int nb = work_blocks();
     return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, nrhs >= 4 ? 4 : 1, nb);
 }
 

@@ -14,6 +14,7 @@
 #include "geom.cuh"
 #include "host_bspline.h"
 #include "iga_internal.cuh"
+#include "leapfrog.cuh"
 #include "stencil.cuh"
 
 namespace iga {
@@ -54,20 +55,38 @@ __global__ void update_kernel(const T* __restrict__ u, T* __restrict__ uprev, co
     }
 }
 
+// FP32 state: compensated update of (hi, lo); uprev / uprevlo receive u^{n+1}
+__global__ void update_comp_kernel(const float* __restrict__ u, const float* __restrict__ ulo, float* __restrict__ uprev,
+                                   float* __restrict__ uprevlo, const float* __restrict__ a, long long n, double dt2,
+                                   int first) {
+    const float c = (float)(first ? 0.5 * dt2 : dt2);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float hn, ln;
+        leapfrog_comp(u[i], ulo[i], uprev[i], uprevlo[i], __fmul_rn(c, a[i]), first != 0, hn, ln);
+        uprev[i] = hn;
+        uprevlo[i] = ln;
+    }
+}
+
+// lo: low parts of a compensated FP32 state (nullptr: none)
 template <typename T>
-__global__ void receiver_kernel(const T* __restrict__ u, const int* __restrict__ idx, const double* __restrict__ w,
-                                double* traces, int nshot, int nrec, int nloc, long long N, int nsteps_max, int step) {
+__global__ void receiver_kernel(const T* __restrict__ u, const T* __restrict__ lo, const int* __restrict__ idx,
+                                const double* __restrict__ w, double* traces, int nshot, int nrec, int nloc, long long N,
+                                int nsteps_max, int step) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;   // (shot, receiver)
     if (k >= nshot * nrec) return;
     const int r = k / nrec, rec = k % nrec;
     double acc = 0.0;
-    for (int l = 0; l < nloc; ++l) acc += w[rec * nloc + l] * (double)u[(size_t)r * N + idx[rec * nloc + l]];
+    for (int l = 0; l < nloc; ++l) {
+        const size_t o = (size_t)r * N + idx[rec * nloc + l];
+        acc += w[rec * nloc + l] * ((double)u[o] + (lo ? (double)lo[o] : 0.0));
+    }
     traces[((size_t)r * nrec + rec) * nsteps_max + step] = acc;
 }
 
 template <typename T>
 __global__ void pulse_kernel(GeomParams gp, const double* __restrict__ greville, const double* __restrict__ centres,
-                             double width, T* u, int nshot, long long N) {
+                             double width, T* u, T* lo, int nshot, long long N) {
     const long long total = (long long)nshot * N;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(k / N);
@@ -82,7 +101,9 @@ __global__ void pulse_kernel(GeomParams gp, const double* __restrict__ greville,
         map_eval(gp, sc, xc, J);
         double d2 = 0.0;
         for (int d = 0; d < gp.dim; ++d) d2 += (x[d] - xc[d]) * (x[d] - xc[d]);
-        u[k] = (T)exp(-d2 / (2.0 * width * width));
+        const double v = exp(-d2 / (2.0 * width * width));
+        u[k] = (T)v;
+        if (lo) lo[k] = (T)(v - (double)(T)v);   // FP32: the rounding error of u^0 starts lo
     }
 }
 
@@ -200,13 +221,22 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
             destroy_events();
             return rc;
         }
-        update_kernel<T><<<ugrid, 256, 0, st>>>(w->u.as<T>(), w->uprev.as<T>(), w->a.as<T>(), tot,
-                                                w->desc.dt * w->desc.dt, n == 0 ? 1 : 0);
-        IGA_LAUNCH_CHECK("update_kernel");
+        if (sizeof(T) == 4) {
+            update_comp_kernel<<<ugrid, 256, 0, st>>>(w->u.as<float>(), w->ulo.as<float>(), w->uprev.as<float>(),
+                                                      w->uprevlo.as<float>(), w->a.as<float>(), tot,
+                                                      w->desc.dt * w->desc.dt, n == 0 ? 1 : 0);
+            IGA_LAUNCH_CHECK("update_comp_kernel");
+            std::swap(w->ulo.ptr, w->uprevlo.ptr);
+        } else {
+            update_kernel<T><<<ugrid, 256, 0, st>>>(w->u.as<T>(), w->uprev.as<T>(), w->a.as<T>(), tot,
+                                                    w->desc.dt * w->desc.dt, n == 0 ? 1 : 0);
+            IGA_LAUNCH_CHECK("update_kernel");
+        }
         std::swap(w->u.ptr, w->uprev.ptr);   // u <- u^{n+1}, uprev <- u^n
         if (w->nrec > 0) {
             const int k = w->nshot * w->nrec;
-            receiver_kernel<T><<<(k + 127) / 128, 128, 0, st>>>(w->u.as<T>(), w->rec_idx.as<int>(), w->rec_w.as<double>(),
+            receiver_kernel<T><<<(k + 127) / 128, 128, 0, st>>>(w->u.as<T>(), sizeof(T) == 4 ? w->ulo.as<T>() : nullptr,
+                                                                w->rec_idx.as<int>(), w->rec_w.as<double>(),
                                                                 w->traces.as<double>(), w->nshot, w->nrec, w->nloc, N,
                                                                 w->desc.nsteps_max, n);
             IGA_LAUNCH_CHECK("receiver_kernel");
@@ -237,6 +267,10 @@ int wave_initial_state(iga_wave* w, cudaStream_t st) {
     const size_t vb = (w->dtype == IGA_F64 ? 8 : 4) * (size_t)w->nshot * w->N;
     IGA_CUDA(cudaMemsetAsync(w->a.ptr, 0, vb, st));
     IGA_CUDA(cudaMemsetAsync(w->uprev.ptr, 0, vb, st));
+    if (w->dtype == IGA_F32) {
+        IGA_CUDA(cudaMemsetAsync(w->ulo.ptr, 0, vb, st));
+        IGA_CUDA(cudaMemsetAsync(w->uprevlo.ptr, 0, vb, st));
+    }
     IGA_CUDA(cudaMemsetAsync(w->traces.ptr, 0, w->traces.bytes, st));
     IGA_CUDA(cudaMemsetAsync(w->counters.ptr, 0, w->counters.bytes, st));
     if (w->desc.init_kind == IGA_INIT_GAUSS_PULSE) {
@@ -244,10 +278,12 @@ int wave_initial_state(iga_wave* w, cudaStream_t st) {
         const int grid = (int)std::min<long long>((tot + 255) / 256, 152 * 16);
         if (w->dtype == IGA_F64)
             pulse_kernel<double><<<grid, 256, 0, st>>>(s->gp, w->greville.as<double>(), w->centres.as<double>(),
-                                                       w->desc.pulse_width, w->u.as<double>(), w->nshot, w->N);
+                                                       w->desc.pulse_width, w->u.as<double>(), nullptr, w->nshot,
+                                                       w->N);
         else
             pulse_kernel<float><<<grid, 256, 0, st>>>(s->gp, w->greville.as<double>(), w->centres.as<double>(),
-                                                      w->desc.pulse_width, w->u.as<float>(), w->nshot, w->N);
+                                                      w->desc.pulse_width, w->u.as<float>(), w->ulo.as<float>(),
+                                                      w->nshot, w->N);
         IGA_LAUNCH_CHECK("pulse_kernel");
     } else {
         IGA_CUDA(cudaMemsetAsync(w->u.ptr, 0, vb, st));
@@ -340,6 +376,8 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
     if (!rc) rc = w->traces.alloc(sizeof(double) * std::max<size_t>(1, (size_t)d.nshot * d.nrec * d.nsteps_max));
     if (!rc) rc = w->counters.alloc(128);
     if (!rc) rc = w->work.alloc(mass_solve_work_bytes(ops, d.dtype, d.nshot));
+    if (!rc && d.dtype == IGA_F32) rc = w->ulo.alloc(vb);
+    if (!rc && d.dtype == IGA_F32) rc = w->uprevlo.alloc(vb);
     if (rc) return bail(rc);
     // source / receiver tables
     std::vector<int> idx;

@@ -26,8 +26,8 @@ IGA_MAP_IDENTITY, IGA_MAP_ANNULUS_QUARTER, IGA_MAP_CUBE_SINE = 0, 1, 2
 IGA_COEF_CONST, IGA_COEF_SINCOS, IGA_COEF_BSPLINE = 0, 1, 2
 IGA_F32, IGA_F64 = 0, 1
 IGA_OP_K, IGA_OP_M = 0, 1
-IGA_TRUE_ONLY, IGA_KEEP_SAMPLES = 1, 2
-IGA_SOLVE_PLAIN = 1
+IGA_TRUE_ONLY, IGA_KEEP_SAMPLES, IGA_MASS_VOLUME_PRESERVING = 1, 2, 4
+IGA_SOLVE_PLAIN, IGA_SOLVE_GRAPH = 1, 2
 IGA_INIT_ZERO, IGA_INIT_GAUSS_PULSE = 0, 1
 
 EXPORTED = [
@@ -38,7 +38,7 @@ EXPORTED = [
     "iga_wave_cg_iterations", "iga_last_error", "iga_launch_count", "iga_wave_reset",
     "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum", "iga_wave_adjoint",
     "iga_batch_create", "iga_batch_destroy", "iga_batch_step", "iga_batch_tune", "iga_batch_partition",
-    "iga_mass_solve_noalloc",
+    "iga_mass_solve_noalloc", "iga_sampling_length_for_mesh",
 ]
 
 
@@ -98,6 +98,7 @@ _sig = {
     "iga_ops_sample_indices": [_vp, C.POINTER(_i)],
     "iga_stencil_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
     "iga_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
+    "iga_sampling_length_for_mesh": [_d, _i, _i, _d, _d, _d, _d, C.POINTER(_i)],
     "iga_mass_solve_noalloc": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_wave_create": [_vp, C.POINTER(iga_wave_desc), C.POINTER(_vp)],
     "iga_wave_destroy": [_vp],
@@ -214,6 +215,12 @@ def iga_ops_sample_indices(ops):
     buf = (C.c_int * max(ns, 1))()
     _check(_lib.iga_ops_sample_indices(ops, buf))
     return np.array(buf[:ns], dtype=np.int64)
+
+
+def iga_sampling_length_for_mesh(h, p, q, a=0.0, b=0.0, C_=1.0, eps=0.1):
+    out = C.c_int()
+    _check(_lib.iga_sampling_length_for_mesh(h, p, q, a, b, C_, eps, C.byref(out)))
+    return out.value
 
 
 # ---- operators -----------------------------------------------------------------

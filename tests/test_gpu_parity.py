@@ -199,7 +199,11 @@ def test_mass_solve_fp64_matches_direct_solve(name):
     assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
-def test_mass_solve_iterates_match_oracle_pcg():
+SCHEDULES = {"persistent": 0, "graph": 2, "plain": 1}
+
+
+@pytest.mark.parametrize("schedule", list(SCHEDULES))
+def test_mass_solve_iterates_match_oracle_pcg(schedule):
     """Fixed iteration count (rtol = 0): GPU and oracle run the identical recurrence."""
     sp, S, SK, SM, _, _ = oracle_full("annulus40_p3_sincos")
     _, ops = gpu_ops("annulus40_p3_sincos")
@@ -209,7 +213,7 @@ def test_mass_solve_iterates_match_oracle_pcg():
     xr, it, _ = pcg(M, b, x0.copy(), 1.0 / M.diagonal(), 0.0, 25)
     bg = torch.tensor(b[None], device="cuda")
     xg = torch.tensor(x0[None], device="cuda")
-    rc, iters, _ = iga.iga_mass_solve(ops, iga.IGA_F64, bg, xg, 1, 0.0, 25)
+    rc, iters, _ = iga.iga_mass_solve(ops, iga.IGA_F64, bg, xg, 1, 0.0, 25, flags=SCHEDULES[schedule])
     assert iters[0] == 25 and it == 25
     assert np.abs(xg.cpu().numpy()[0] - xr).max() <= 1e-11 * np.abs(xr).max()
 
@@ -230,20 +234,46 @@ def test_mass_solve_plain_and_persistent_schedules_agree_bitwise(dtype):
     assert torch.equal(x1, x2)
 
 
-def test_mass_solve_zero_rhs_gives_zero():
+@pytest.mark.parametrize("schedule", list(SCHEDULES))
+def test_mass_solve_zero_rhs_gives_zero(schedule):
     _, ops = gpu_ops("annulus64_p2")
     b = torch.zeros((1, 4356), dtype=torch.float64, device="cuda")
     x = torch.ones_like(b)
-    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, b, x, 1, 1e-10, 100)
+    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, b, x, 1, 1e-10, 100, flags=SCHEDULES[schedule])
     assert iters[0] == 0 and float(x.abs().max()) == 0.0
 
 
-def test_mass_solve_reports_non_convergence():
+@pytest.mark.parametrize("schedule", list(SCHEDULES))
+def test_mass_solve_reports_non_convergence(schedule):
     _, ops = gpu_ops("annulus64_p2")
     b = torch.tensor(inputs.vectors(4356, 1), device="cuda")
     x = torch.zeros_like(b)
-    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, b, x, 1, 1e-12, 2, allow_not_converged=True)
+    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F64, b, x, 1, 1e-12, 2, flags=SCHEDULES[schedule],
+                                        allow_not_converged=True)
     assert rc == iga.IGA_ERR_NOT_CONVERGED and iters[0] == 2 and rel[0] > 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_mass_solve_graph_schedule_matches_persistent(dtype):
+    """Same recurrence, different block partition of the dot products: results agree to
+    the CG tolerance scale and the iteration counts to within one."""
+    _, ops = gpu_ops("cube20_p2_theta")
+    info = iga.iga_ops_info_get(ops)
+    dt = iga.IGA_F64 if dtype == "f64" else iga.IGA_F32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    b = torch.tensor(inputs.vectors(info.N, 5), dtype=tdt, device="cuda")   # a 4-wide and a 1-wide chunk
+    x1 = torch.zeros_like(b)
+    x2 = torch.zeros_like(b)
+    rtol = 1e-12 if dtype == "f64" else 1e-6
+    _, i1, r1 = iga.iga_mass_solve(ops, dt, b, x1, 5, rtol, 500)
+    _, i2, r2 = iga.iga_mass_solve(ops, dt, b, x2, 5, rtol, 500, flags=iga.IGA_SOLVE_GRAPH)
+    assert np.all(np.abs(i1 - i2) <= 1) and np.all(r2 <= rtol)
+    tol = 1e-10 if dtype == "f64" else 2e-5
+    assert float((x1 - x2).abs().max()) <= tol * float(x1.abs().max())
+    # deterministic: a second graph solve is bitwise identical
+    x3 = torch.zeros_like(b)
+    _, i3, _ = iga.iga_mass_solve(ops, dt, b, x3, 5, rtol, 500, flags=iga.IGA_SOLVE_GRAPH)
+    assert list(i3) == list(i2) and torch.equal(x3, x2)
 
 
 def _wave_case(dtype, nsteps=20):
@@ -287,7 +317,7 @@ def test_wave_fp32_error_against_fp64_oracle():
     assert err <= 1e-5
 
 
-@pytest.mark.parametrize("mode", ["f64", "f64_plain", "f32"])
+@pytest.mark.parametrize("mode", ["f64", "f64_plain", "f64_graph", "f32", "f32_graph"])
 def test_wave_cube_ricker_source_matches_oracle(mode):
     """3-D, lognormal wave speed, Ricker point source at the centre (the bench workload family)."""
     name = "cube20_p2_theta_M2"
@@ -298,13 +328,15 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     nsteps = 60
     src = W.source_position(w)
     rec = np.array([src + [0.05, 0.0, 0.0], src + [0.0, -0.1, 0.05]])
-    dtype = iga.IGA_F32 if mode == "f32" else iga.IGA_F64
-    flags = iga.IGA_SOLVE_PLAIN if mode == "f64_plain" else 0
+    f32 = mode.startswith("f32")
+    dtype = iga.IGA_F32 if f32 else iga.IGA_F64
+    flags = {"f64_plain": iga.IGA_SOLVE_PLAIN, "f64_graph": iga.IGA_SOLVE_GRAPH,
+             "f32_graph": iga.IGA_SOLVE_GRAPH}.get(mode, 0)
     wave = iga.iga_wave_create(ops, 1, dtype, dt, src_pos=src[None], f0=10.0, t0=0.1, rec_pos=rec,
-                               nsteps_max=nsteps, cg_rtol=1e-6 if mode == "f32" else 1e-13,
+                               nsteps_max=nsteps, cg_rtol=1e-6 if f32 else 1e-13,
                                cg_max_it=3000, solve_flags=flags)
     iga.iga_wave_step(wave, nsteps)
-    tdt = torch.float32 if mode == "f32" else torch.float64
+    tdt = torch.float32 if f32 else torch.float64
     u = torch.empty((1, sp.N), dtype=tdt, device="cuda")
     iga.iga_wave_get_state(wave, u)
     torch.cuda.synchronize()
@@ -318,7 +350,7 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     print(mode, "relative L2 error", err, "trace error", terr)
     # FP32 parity tolerance 2e-5: storing M~ in FP32 perturbs each solve by about
     # cond(M~) * 2^-24 ~ 1e-5 whatever the CG tolerance
-    tol = 2e-5 if mode == "f32" else 1e-11
+    tol = 2e-5 if f32 else 1e-11
     assert err <= tol and terr <= tol
 
 
