@@ -98,6 +98,57 @@ __device__ __forceinline__ void stencil_row(const T* __restrict__ F, long long p
     }
 }
 
+// One row computed by a whole warp: the fields are split across the lanes
+// (u = lane, lane + 32, ..) with the same clamped neighbour handling as
+// stencil_row, then summed with a fixed butterfly, so every lane returns the row.
+// Used for the few rows left after the last full round of a grid-stride loop,
+// where one thread per row would leave the rest of the grid waiting on a single
+// row's chain of field loads.  All 32 lanes must call it together.
+template <int DIM, int P, typename T, bool MASS, int R, class Load>
+__device__ __forceinline__ void stencil_row_warp(const T* __restrict__ F, long long pitch, const Load& ld, int i, int N,
+                                                 int m, int lane, T* acc, T* own) {
+    constexpr int NF = StencilShape<DIM, P>::T0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) own[r] = ld(r, i);
+    if (MASS) {
+        const T d = lane == 0 ? __ldg(F + i) : T(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = d * own[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = T(0);
+    }
+    const T* Foff = MASS ? F + pitch : F;
+    for (int u = lane; u < NF; u += 32) {
+        const int dl = field_delta<DIM, P>(u, m);
+        const T* Fu = Foff + (size_t)u * pitch;
+        const int ip = i + dl, im = i - dl;
+        const bool okp = ip < N, okm = im >= 0;
+        const int ipc = okp ? ip : i, imc = okm ? im : i;
+        const T s = __ldg(Fu + i);
+        const T smv = __ldg(Fu + imc);
+        const T sm = okm ? smv : T(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T xpv = ld(r, ipc);
+            const T xmv = ld(r, imc);
+            const T xp = okp ? xpv : T(0);
+            const T xm = okm ? xmv : T(0);
+            if (MASS) {
+                acc[r] = fma(s, xp, acc[r]);
+                acc[r] = fma(sm, xm, acc[r]);
+            } else {
+                acc[r] = fma(s, xp - own[r], acc[r]);
+                acc[r] = fma(sm, xm - own[r], acc[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
 // Interior rows (Delta_max <= i < N - Delta_max): every neighbour is inside
 // [0, N), so no clamping or masking is needed.  Offsets come from the shared
 // table sdl[u] = Delta_u (one broadcast load per field); per field and RHS the

@@ -1,8 +1,11 @@
-"""Small profiling cases for ncu: K~ applies and a short fixed-iteration PCG solve.
+"""Small profiling cases for ncu: K~ applies and fixed-iteration PCG solves.
 
     python -m paper_2004_05197_gb300.profile_cases [n_el]
 
 Workload: the cube96_p2 family at n_el (default 80: the FP32 fields exceed L2).
+Launch order: two K~ applies, then persistent PCG solves of exactly 10, 10 and 20
+iterations (rtol 0), so that a capture of the last two separates the per-solve
+and per-iteration DRAM traffic.
 """
 import sys
 
@@ -22,9 +25,9 @@ def main(n_el=80):
     y = torch.empty_like(x)
     for _ in range(2):
         iga.iga_stencil_apply(ops, iga.IGA_OP_K, iga.IGA_F32, x, y, 1)
-    for _ in range(2):
+    for its in (10, 10, 20):
         a = torch.zeros_like(x)
-        iga.iga_mass_solve(ops, iga.IGA_F32, x, a, 1, 0.0, 10)
+        iga.iga_mass_solve(ops, iga.IGA_F32, x, a, 1, 0.0, its)
     torch.cuda.synchronize()
     print("ok N", N)
 
