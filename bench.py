@@ -43,6 +43,34 @@ def load_peaks():
         return None
 
 
+PCG_PROFILE = os.path.join(ROOT, "profiles", "stencil_apply_and_pcg_cube80_p2.md")
+PCG_SOURCES = ["solve.cu", "cg.cuh", "stencil.cuh"]
+
+
+def pcg_profiled_traffic():
+    """DRAM bytes per row (per solve, per iteration) of the persistent PCG from the
+    committed ncu summary, or None when the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        vals = {}
+        with open(PCG_PROFILE) as f:
+            for line in f:
+                line = line.strip()
+                for key in ("pcg_dram_bytes_per_row_init", "pcg_dram_bytes_per_row_iteration",
+                            "kernel_sources_sha256_16"):
+                    if line.startswith(key + ":"):
+                        vals[key] = line.split(":", 1)[1].strip()
+        h = hashlib.sha256()
+        for name in PCG_SOURCES:
+            with open(os.path.join(ROOT, "paper_2004_05197_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != vals.get("kernel_sources_sha256_16"):
+            return None
+        return float(vals["pcg_dram_bytes_per_row_init"]), float(vals["pcg_dram_bytes_per_row_iteration"])
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
 
@@ -200,6 +228,12 @@ def run_ours(args, rank, world, device):
     # one shot: every launch is one solve and the device counter holds its iterations
     cg_bytes_total = (cg_solves * init_b + cg_it * it_b) * N if args.nshot == 1 else None
     achieved = cg_bytes_total / (cg_ms / 1e3) / 1e9 if cg_bytes_total else None
+    # ncu DRAM bytes of the same kernel on the n_el = 80 case, scaled to this launch by rows
+    # and by the mean iterations per launch (traffic grows in proportion to both)
+    prof = pcg_profiled_traffic() if (args.nshot == 1 and args.solve == "persistent") else None
+    traffic = ((prof[0] + prof[1] * cg_it / max(1, cg_solves)) * N) if prof else None
+    traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, %s, scaled by rows and "
+                   "iterations per launch" % os.path.relpath(PCG_PROFILE, ROOT)) if prof else None
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs") if peaks else None
     peak_src = "measured" if peak else "fallback"
@@ -232,7 +266,8 @@ def run_ours(args, rank, world, device):
                                 else "pcg_persistent_kernel"),
                      "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": traffic_src,
                      "bytes_per_row_per_iteration": it_b, "launches": cg_solves,
                      "avg_launch_ms": cg_ms / max(1, cg_solves)},
         "gpu_launches": launches,
