@@ -41,6 +41,29 @@ class AnnulusQuarter:
         return x, J
 
 
+class AnnulusSector:
+    """F(s,t) = (r cos a, r sin a), r = r0 + (r1 - r0) s, a = a0 + (a1 - a0) t: one patch of
+    an annulus split into sectors (multi-patch remark of Sec. 3.2); r0 = 1, r1 = 2, a0 = 0,
+    a1 = pi/2 is the quarter annulus."""
+    dim = 2
+
+    def __init__(self, r0=1.0, r1=2.0, a0=0.0, a1=0.5 * np.pi):
+        self.r0, self.r1, self.a0, self.a1 = r0, r1, a0, a1
+
+    def __call__(self, s):
+        s = np.asarray(s, dtype=np.float64)
+        dr, da = self.r1 - self.r0, self.a1 - self.a0
+        r = self.r0 + dr * s[..., 0]
+        a = self.a0 + da * s[..., 1]
+        x = np.stack([r * np.cos(a), r * np.sin(a)], axis=-1)
+        J = np.empty(s.shape + (2,))
+        J[..., 0, 0] = dr * np.cos(a)
+        J[..., 0, 1] = -r * da * np.sin(a)
+        J[..., 1, 0] = dr * np.sin(a)
+        J[..., 1, 1] = r * da * np.cos(a)
+        return x, J
+
+
 class CubeSinePerturbed:
     """x_k = s_k + eps * sin(pi s) sin(pi t) sin(pi u) for each coordinate k (unit cube)."""
     dim = 3
