@@ -61,6 +61,9 @@ extern "C" {
 #define IGA_MAP_IDENTITY         0  /* F(s) = s */
 #define IGA_MAP_ANNULUS_QUARTER  1  /* F(s,t) = ((1+s) cos(pi t/2), (1+s) sin(pi t/2)) */
 #define IGA_MAP_CUBE_SINE        2  /* x_k = s_k + a sin(pi s) sin(pi t) sin(pi u), a = map_param */
+#define IGA_MAP_ANNULUS_SECTOR   3  /* F(s,t) = (r cos a, r sin a), r = r0 + (r1-r0) s,
+                                       a = a0 + (a1-a0) t, (r0, r1, a0, a1) = sector[]: one patch of
+                                       a multi-patch annulus; det J = (r1-r0)(a1-a0) r must be > 0 */
 
 #define IGA_COEF_CONST    0  /* c = coef_param */
 #define IGA_COEF_SINCOS   1  /* c(x) = 1 + coef_param sin(2 pi x_1) cos(2 pi x_2), x = F(s) physical */
@@ -117,6 +120,7 @@ typedef struct iga_space_desc {
     int n_theta;           /* BSPLINE: coefficients per direction (> theta_degree) */
     int theta_degree;      /* BSPLINE: degree of the coefficient spline, 1..5 */
     int quad_pts;          /* Gauss points per direction and element; 0 => p+1 (Sec. 5.1); <= 8 */
+    double sector[4];      /* ANNULUS_SECTOR: r0, r1, a0, a1 (radians) */
 } iga_space_desc;
 
 typedef struct iga_space_info {
@@ -343,6 +347,48 @@ int iga_batch_partition(const iga_batch* batch, int* blocks_out);
  * 1..nsteps_max, coefficient not a B-spline), CG errors as in wave_step. */
 int iga_wave_adjoint(iga_wave* wave, int nsteps, int checkpoint_every, const double* obs, double* J_out,
                      double* grad_theta, void* stream);
+
+/* ---- multi-patch ---------------------------------------------------------
+ * Sec. 3.2 and Sec. 3.4 (remarks on multi-patch geometries): a domain split into
+ * 2-D patches, each with its own map, coefficient and surrogate fields (one
+ * iga_ops per patch, assembled on its own space), glued along whole sides into
+ * the C0-conforming multi-patch space.  The global matrix is the sum over
+ * patches of P_l^T A_l P_l.  Global numbering: the local functions are visited
+ * patch by patch, each patch in colex order, and every class of functions
+ * identified by the interfaces takes the next global index at its first member.
+ */
+typedef struct iga_multipatch iga_multipatch;
+typedef struct iga_interface {
+    int patch_a, side_a;   /* side: 0 = {i_1 = 0}, 1 = {i_1 = m-1}, 2 = {i_2 = 0}, 3 = {i_2 = m-1} */
+    int patch_b, side_b;   /* the two sides must have the same number m of functions */
+    int reversed;          /* 0: entry k meets entry k; 1: entry k meets entry m-1-k
+                              (entries ordered by the other index along the side) */
+} iga_interface;
+
+/* patches: npatch borrowed iga_ops (2-D, same p; they must outlive the handle).
+ * Builds the numbering and the inverse Jacobi diagonal of the global M~.
+ * Errors: IGA_ERR_ARG (bad interface, unequal sides, 3-D patch),
+ * IGA_ERR_NONFINITE (non-positive global mass diagonal).  Synchronous. */
+int iga_multipatch_create(int npatch, const iga_ops* const* patches, int ninterface,
+                          const iga_interface* interfaces, iga_multipatch** out);
+int iga_multipatch_destroy(iga_multipatch* mp);
+/* Number of global functions.  Host only. */
+int iga_multipatch_size(const iga_multipatch* mp, long long* n_global);
+/* Global index of every local function of `patch` (colex), into host_map[N_patch]. */
+int iga_multipatch_global_index(const iga_multipatch* mp, int patch, long long* host_map);
+/* y = A x for the global K~ or M~; x, y device [nrhs][n_global] of dtype (y must not
+ * alias x).  Gathers the patch vectors, applies every patch operator, sums the
+ * patch results of every global function in a fixed order.  Async on stream. */
+int iga_multipatch_apply(const iga_multipatch* mp, int which, int dtype, const void* x, void* y,
+                         int nrhs, void* stream);
+/* Jacobi-PCG on the global M~ a = b, b / x device [nrhs][n_global] (x: initial guess
+ * in, solution out), stop when ||r||_2 <= rtol ||b||_2; FP32 dtype: FP32 vectors,
+ * FP64 residual and dot products.  Host-driven (plain schedule: scalars read back
+ * every iteration), synchronous.  Returns IGA_ERR_NOT_CONVERGED / IGA_ERR_NONFINITE
+ * as mass_solve. */
+int iga_multipatch_mass_solve(const iga_multipatch* mp, int dtype, const void* b, void* x, int nrhs,
+                              double rtol, int max_it, int* iters_out, double* relres_out,
+                              void* stream);
 
 /* ---- misc ------------------------------------------------------------- */
 const char* iga_last_error(void);

@@ -34,6 +34,17 @@ __device__ inline void map_eval(const GeomParams& gp, const double* s, double* x
         J[0][1] = -r * hp * sn;
         J[1][0] = sn;
         J[1][1] = r * hp * cs;
+    } else if (gp.map_kind == IGA_MAP_ANNULUS_SECTOR) {
+        const double dr = gp.sector[1] - gp.sector[0], da = gp.sector[3] - gp.sector[2];
+        const double r = gp.sector[0] + dr * s[0];
+        double sn, cs;
+        sincos(gp.sector[2] + da * s[1], &sn, &cs);
+        x[0] = r * cs;
+        x[1] = r * sn;
+        J[0][0] = dr * cs;
+        J[0][1] = -r * da * sn;
+        J[1][0] = dr * sn;
+        J[1][1] = r * da * cs;
     } else if (gp.map_kind == IGA_MAP_CUBE_SINE) {
         double sn[3], cs[3];
         for (int k = 0; k < 3; ++k) sincospi(s[k], &sn[k], &cs[k]);

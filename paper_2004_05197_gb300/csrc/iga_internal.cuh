@@ -40,6 +40,7 @@ struct GeomParams {
     int dim, p, n_el, m, nq;
     int map_kind;
     double map_param;
+    double sector[4];      // ANNULUS_SECTOR: r0, r1, a0, a1
     int coef_kind;
     double coef_param;
     const double* theta;   // [n_theta^dim] colex

@@ -1,0 +1,504 @@
+// Multi-patch operators (Sec. 3.2 and Sec. 3.4, remarks on multi-patch
+// geometries): every patch keeps its own surrogate fields (its own stencil
+// functions, assembled by iga_surrogate_assemble on its own space), and the
+// global matrix of the C0-conforming multi-patch space is the sum over patches of
+// P_l^T A_l P_l, P_l the map from global to patch-local coefficients.
+//
+// Applied matrix-free: gather the patch-local vectors, apply every patch's
+// stencil operator with the single-patch kernels, and sum the patch results of
+// every global function in a fixed order (a function on a shared side belongs
+// to two or more patches).  The mass solve is Jacobi-PCG on the global system,
+// host-driven (two scalar read-backs per iteration): the plain schedule.
+//
+// Global numbering: local functions visited patch by patch, each patch in
+// colexicographic order; the side functions identified by the interfaces form
+// classes, and a class takes the next global index at its first member.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "iga_internal.cuh"
+
+struct iga_multipatch {
+    std::vector<const iga_ops*> patches;
+    std::vector<long long> off, n;           // patch-local offsets (concatenated) and sizes
+    long long G = 0, L = 0;                  // global and total local counts
+    std::vector<long long> l2g_h;            // [L] global index of every local function
+    iga::DevBuf l2g;                         // int [L]
+    iga::DevBuf gptr, gpatch, glocal;        // CSR global -> (patch, local index), int
+    iga::DevBuf poff, pn;                    // long long [npatch]
+    iga::DevBuf dinv64, dinv32;              // inverse Jacobi diagonal of the global M~
+    iga::DevBuf work;                        // per-call scratch (grown on demand)
+};
+
+namespace iga {
+namespace {
+
+long long side_index(int m, int side, int k) {
+    switch (side) {
+        case 0: return (long long)k * m;
+        case 1: return (long long)k * m + (m - 1);
+        case 2: return k;
+        default: return (long long)(m - 1) * m + k;
+    }
+}
+
+long long uf_find(std::vector<long long>& parent, long long a) {
+    while (parent[a] != a) {
+        parent[a] = parent[parent[a]];
+        a = parent[a];
+    }
+    return a;
+}
+
+// x_l[r][i] = x[r][l2g[off + i]] for the rows of one patch (patch-major layout)
+template <typename T>
+__global__ void mp_gather_kernel(const T* __restrict__ x, long long G, const int* __restrict__ l2g, long long off,
+                                 long long n, T* __restrict__ xl, int R) {
+    const long long tot = (long long)R * n;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot; k += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(k / n);
+        const long long i = k % n;
+        xl[k] = x[(long long)r * G + l2g[off + i]];
+    }
+}
+
+// y[r][g] = sum over the (patch, local) entries of g, in CSR order, of y_l
+template <typename T>
+__global__ void mp_scatter_kernel(const T* __restrict__ yl, const int* __restrict__ gptr, const int* __restrict__ gpatch,
+                                  const int* __restrict__ glocal, const long long* __restrict__ poff,
+                                  const long long* __restrict__ pn, long long G, int R, T* __restrict__ y) {
+    const long long tot = (long long)R * G;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot; k += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(k / G);
+        const long long g = k % G;
+        T s = T(0);
+        for (int j = gptr[g]; j < gptr[g + 1]; ++j) {
+            const int l = gpatch[j];
+            s += yl[(long long)R * poff[l] + (long long)r * pn[l] + glocal[j]];
+        }
+        y[k] = s;
+    }
+}
+
+// global diagonal of M~: sum of the patch diagonals (field 0 of every patch's M~)
+__global__ void mp_diag_kernel(const double* const* __restrict__ fm, const int* __restrict__ gptr,
+                               const int* __restrict__ gpatch, const int* __restrict__ glocal, long long G,
+                               double* dinv64, float* dinv32, int* bad) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int j = gptr[g]; j < gptr[g + 1]; ++j) d += fm[gpatch[j]][glocal[j]];
+        if (!(d > 0.0)) atomicOr(bad, 1);
+        dinv64[g] = 1.0 / d;
+        dinv32[g] = (float)(1.0 / d);
+    }
+}
+
+constexpr int kMpThreads = 256;
+constexpr int kMpBlocks = 152 * 8;
+
+// per-block FP64 partial sums of K dot products over [R][G] vectors (fixed order)
+template <int K>
+__device__ __forceinline__ void mp_block_partials(double (&v)[K], double* out) {
+    __shared__ double ws[kMpThreads / 32][K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) ws[w][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int q = 0; q < kMpThreads / 32; ++q) s += ws[q][threadIdx.x];
+        out[(size_t)blockIdx.x * K + threadIdx.x] = s;
+    }
+}
+
+// partials[b][r] of (p_r, q_r)
+template <typename T>
+__global__ void __launch_bounds__(kMpThreads) mp_dot_kernel(const T* __restrict__ p, const T* __restrict__ q, long long G,
+                                                            int r, double* partials) {
+    double v[1] = {0.0};
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x)
+        v[0] += (double)p[(long long)r * G + g] * (double)q[(long long)r * G + g];
+    mp_block_partials<1>(v, partials);
+}
+
+// x += alpha p, r -= alpha q, z = D^-1 r; partials (r, r), (r, z) of one right-hand side
+template <typename T>
+__global__ void __launch_bounds__(kMpThreads) mp_update_kernel(T* x, double* res, T* z, const T* __restrict__ p,
+                                                               const T* __restrict__ q, const T* __restrict__ dinv,
+                                                               long long G, int r, double alpha, double* partials) {
+    double v[2] = {0.0, 0.0};
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long o = (long long)r * G + g;
+        x[o] = x[o] + (T)alpha * p[o];
+        const double ri = res[o] - alpha * (double)q[o];
+        res[o] = ri;
+        const T zi = (T)((double)dinv[g] * ri);
+        z[o] = zi;
+        v[0] += ri * ri;
+        v[1] += ri * (double)zi;
+    }
+    mp_block_partials<2>(v, partials);
+}
+
+// r = b - q (q = A x), z = D^-1 r, p = z; partials (r, r), (r, z), (b, b)
+template <typename T>
+__global__ void __launch_bounds__(kMpThreads) mp_init_kernel(const T* __restrict__ b, const T* __restrict__ q, double* res,
+                                                             T* z, T* p, const T* __restrict__ dinv, long long G, int r,
+                                                             double* partials) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long o = (long long)r * G + g;
+        const double bi = (double)b[o];
+        const double ri = bi - (double)q[o];
+        res[o] = ri;
+        const T zi = (T)((double)dinv[g] * ri);
+        z[o] = zi;
+        p[o] = zi;
+        v[0] += ri * ri;
+        v[1] += ri * (double)zi;
+        v[2] += bi * bi;
+    }
+    mp_block_partials<3>(v, partials);
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void mp_dir_kernel(T* p, const T* __restrict__ z, long long G, int r, double beta) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long o = (long long)r * G + g;
+        p[o] = z[o] + (T)beta * p[o];
+    }
+}
+
+// out[k] = sum over blocks of partials[b][k], fixed order (one block)
+template <int K>
+__global__ void mp_reduce_kernel(const double* __restrict__ partials, int nb, double* out) {
+    __shared__ double ws[kMpThreads / 32][K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[(size_t)b * K + k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) ws[w][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int q = 0; q < kMpThreads / 32; ++q) s += ws[q][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+}  // namespace
+}  // namespace iga
+
+using namespace iga;
+
+extern "C" int iga_multipatch_create(int npatch, const iga_ops* const* patches, int ninterface,
+                                     const iga_interface* ifs, iga_multipatch** out) {
+    if (!out || npatch < 1 || !patches || ninterface < 0 || (ninterface > 0 && !ifs))
+        return fail(IGA_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    for (int l = 0; l < npatch; ++l) {
+        if (!patches[l]) return fail(IGA_ERR_ARG, "null patch");
+        if (patches[l]->dim != 2) return fail(IGA_ERR_ARG, "multi-patch gluing is implemented for 2-D patches");
+        if (patches[l]->p != patches[0]->p) return fail(IGA_ERR_ARG, "patches must share the degree p");
+    }
+    iga_multipatch* mp = new (std::nothrow) iga_multipatch();
+    if (!mp) return fail(IGA_ERR_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        delete mp;
+        return rc;
+    };
+    mp->patches.assign(patches, patches + npatch);
+    mp->off.resize(npatch);
+    mp->n.resize(npatch);
+    long long L = 0;
+    for (int l = 0; l < npatch; ++l) {
+        mp->off[l] = L;
+        mp->n[l] = patches[l]->N;
+        L += patches[l]->N;
+    }
+    if (L > (1LL << 31) - 1) return bail(fail(IGA_ERR_ARG, "too many local functions for 32-bit indexing"));
+    mp->L = L;
+    // union-find over the local functions; the class representative is its smallest member
+    std::vector<long long> parent(L);
+    std::iota(parent.begin(), parent.end(), 0LL);
+    for (int f = 0; f < ninterface; ++f) {
+        const iga_interface& it = ifs[f];
+        if (it.patch_a < 0 || it.patch_a >= npatch || it.patch_b < 0 || it.patch_b >= npatch ||
+            it.side_a < 0 || it.side_a > 3 || it.side_b < 0 || it.side_b > 3)
+            return bail(fail(IGA_ERR_ARG, "interface names a patch or side that does not exist"));
+        const int ma = patches[it.patch_a]->m, mb = patches[it.patch_b]->m;
+        if (ma != mb) return bail(fail(IGA_ERR_ARG, "glued sides need the same number of functions"));
+        if (it.patch_a == it.patch_b && it.side_a == it.side_b)
+            return bail(fail(IGA_ERR_ARG, "a side cannot be glued to itself"));
+        for (int k = 0; k < ma; ++k) {
+            const long long a = mp->off[it.patch_a] + side_index(ma, it.side_a, k);
+            const long long b = mp->off[it.patch_b] + side_index(mb, it.side_b, it.reversed ? ma - 1 - k : k);
+            const long long ra = uf_find(parent, a), rb = uf_find(parent, b);
+            if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+        }
+    }
+    mp->l2g_h.assign(L, -1);
+    std::vector<long long> cls(L, -1);
+    long long G = 0;
+    for (long long k = 0; k < L; ++k) {
+        const long long r = uf_find(parent, k);
+        if (cls[r] < 0) cls[r] = G++;
+        mp->l2g_h[k] = cls[r];
+    }
+    mp->G = G;
+    // CSR global -> (patch, local), members in visiting order
+    std::vector<int> cnt(G + 1, 0), gpatch(L), glocal(L), l2g32(L);
+    for (long long k = 0; k < L; ++k) cnt[mp->l2g_h[k] + 1] += 1;
+    for (long long g = 0; g < G; ++g) cnt[g + 1] += cnt[g];
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int l = 0; l < npatch; ++l)
+        for (long long i = 0; i < mp->n[l]; ++i) {
+            const long long k = mp->off[l] + i;
+            const long long g = mp->l2g_h[k];
+            gpatch[fill[g]] = l;
+            glocal[fill[g]] = (int)i;
+            ++fill[g];
+            l2g32[k] = (int)g;
+        }
+    int rc = mp->l2g.alloc(sizeof(int) * L);
+    if (!rc) rc = mp->gptr.alloc(sizeof(int) * (G + 1));
+    if (!rc) rc = mp->gpatch.alloc(sizeof(int) * L);
+    if (!rc) rc = mp->glocal.alloc(sizeof(int) * L);
+    if (!rc) rc = mp->poff.alloc(sizeof(long long) * npatch);
+    if (!rc) rc = mp->pn.alloc(sizeof(long long) * npatch);
+    if (!rc) rc = mp->dinv64.alloc(sizeof(double) * G);
+    if (!rc) rc = mp->dinv32.alloc(sizeof(float) * G);
+    if (rc) return bail(rc);
+    DevBuf fm, bad;
+    std::vector<const double*> fm_h(npatch);
+    for (int l = 0; l < npatch; ++l) fm_h[l] = patches[l]->fM64.as<double>();
+    if ((rc = fm.alloc(sizeof(double*) * npatch)) || (rc = bad.alloc(sizeof(int)))) return bail(rc);
+    cudaError_t e = cudaMemcpy(mp->l2g.ptr, l2g32.data(), sizeof(int) * L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(mp->gptr.ptr, cnt.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(mp->gpatch.ptr, gpatch.data(), sizeof(int) * L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(mp->glocal.ptr, glocal.data(), sizeof(int) * L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(mp->poff.ptr, mp->off.data(), sizeof(long long) * npatch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(mp->pn.ptr, mp->n.data(), sizeof(long long) * npatch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fm.ptr, fm_h.data(), sizeof(double*) * npatch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(bad.ptr, 0, sizeof(int));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "multipatch upload"));
+    const int grid = (int)std::min<long long>((G + 255) / 256, kMpBlocks);
+    mp_diag_kernel<<<grid, 256>>>(fm.as<const double*>(), mp->gptr.as<int>(), mp->gpatch.as<int>(),
+                                  mp->glocal.as<int>(), G, mp->dinv64.as<double>(), mp->dinv32.as<float>(),
+                                  bad.as<int>());
+    count_launch();
+    int bad_h = 0;
+    e = cudaMemcpy(&bad_h, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "mp_diag_kernel"));
+    if (bad_h) return bail(fail(IGA_ERR_NONFINITE, "non-positive global mass diagonal"));
+    *out = mp;
+    return IGA_OK;
+}
+
+extern "C" int iga_multipatch_destroy(iga_multipatch* mp) {
+    delete mp;
+    return IGA_OK;
+}
+
+extern "C" int iga_multipatch_size(const iga_multipatch* mp, long long* n_global) {
+    if (!mp || !n_global) return fail(IGA_ERR_ARG, "null argument");
+    *n_global = mp->G;
+    return IGA_OK;
+}
+
+extern "C" int iga_multipatch_global_index(const iga_multipatch* mp, int patch, long long* host_map) {
+    if (!mp || !host_map) return fail(IGA_ERR_ARG, "null argument");
+    if (patch < 0 || patch >= (int)mp->patches.size()) return fail(IGA_ERR_ARG, "no such patch");
+    std::memcpy(host_map, mp->l2g_h.data() + mp->off[patch], sizeof(long long) * mp->n[patch]);
+    return IGA_OK;
+}
+
+namespace iga {
+namespace {
+
+// Scratch carve: x_l, y_l [R][L] (dtype), res [R][G] FP64, z, p, q [R][G] (dtype),
+// partials [kMpBlocks][3] and reduced scalars [R][3] FP64.
+struct MpWork {
+    void *xl, *yl, *z, *p, *q;
+    double *res, *partials, *red;
+};
+
+size_t mp_work_bytes(const iga_multipatch* mp, size_t es, int R) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    return 2 * up(es * R * mp->L) + up(8 * (size_t)R * mp->G) + 3 * up(es * R * mp->G) + up(8 * kMpBlocks * 3) +
+           up(8 * 3 * (size_t)R) + 256;
+}
+
+int mp_work(const iga_multipatch* mp, size_t es, int R, MpWork& w) {
+    iga_multipatch* m = const_cast<iga_multipatch*>(mp);
+    const size_t need = mp_work_bytes(mp, es, R);
+    if (m->work.bytes < need) {
+        int rc = m->work.alloc(need);
+        if (rc) return rc;
+    }
+    char* p = (char*)m->work.ptr;
+    auto take = [&](size_t b) {
+        void* o = p;
+        p += (b + 255) / 256 * 256;
+        return o;
+    };
+    w.xl = take(es * R * mp->L);
+    w.yl = take(es * R * mp->L);
+    w.res = (double*)take(8 * (size_t)R * mp->G);
+    w.z = take(es * R * mp->G);
+    w.p = take(es * R * mp->G);
+    w.q = take(es * R * mp->G);
+    w.partials = (double*)take(8 * kMpBlocks * 3);
+    w.red = (double*)take(8 * 3 * (size_t)R);
+    return IGA_OK;
+}
+
+template <typename T>
+int mp_apply_typed(const iga_multipatch* mp, int which, const T* x, T* y, int R, cudaStream_t st, const MpWork& w) {
+    T* xl = (T*)w.xl;
+    T* yl = (T*)w.yl;
+    for (size_t l = 0; l < mp->patches.size(); ++l) {
+        const long long n = mp->n[l], base = (long long)R * mp->off[l];
+        const int grid = (int)std::min<long long>((R * n + 255) / 256, kMpBlocks);
+        mp_gather_kernel<T><<<grid, 256, 0, st>>>(x, mp->G, mp->l2g.as<int>(), mp->off[l], n, xl + base, R);
+        IGA_LAUNCH_CHECK("mp_gather_kernel");
+        int rc = launch_apply(mp->patches[l], which, sizeof(T) == 8 ? IGA_F64 : IGA_F32, xl + base, yl + base, R, st);
+        if (rc) return rc;
+    }
+    const int grid = (int)std::min<long long>(((long long)R * mp->G + 255) / 256, kMpBlocks);
+    mp_scatter_kernel<T><<<grid, 256, 0, st>>>(yl, mp->gptr.as<int>(), mp->gpatch.as<int>(), mp->glocal.as<int>(),
+                                               mp->poff.as<long long>(), mp->pn.as<long long>(), mp->G, R, y);
+    IGA_LAUNCH_CHECK("mp_scatter_kernel");
+    return IGA_OK;
+}
+
+template <typename T>
+int mp_solve_typed(const iga_multipatch* mp, const T* b, T* x, int R, double rtol, int max_it, int* iters_out,
+                   double* relres_out, cudaStream_t st) {
+    MpWork w;
+    int rc = mp_work(mp, sizeof(T), R, w);
+    if (rc) return rc;
+    const long long G = mp->G;
+    const T* dinv = sizeof(T) == 8 ? (const T*)mp->dinv64.ptr : (const T*)mp->dinv32.ptr;
+    T* z = (T*)w.z;
+    T* p = (T*)w.p;
+    T* q = (T*)w.q;
+    const int grid = (int)std::min<long long>((G + kMpThreads - 1) / kMpThreads, kMpBlocks);
+    std::vector<double> red(3 * (size_t)R), rz(R), rr(R), bn(R);
+    std::vector<int> active(R), iters(R, 0);
+    auto reduce_all = [&]() -> int {   // reduced scalars [R][3] to the host
+        IGA_CUDA(cudaMemcpyAsync(red.data(), w.red, sizeof(double) * 3 * R, cudaMemcpyDeviceToHost, st));
+        IGA_CUDA(cudaStreamSynchronize(st));
+        return IGA_OK;
+    };
+    // r = b - A x, z = D^-1 r, p = z
+    if ((rc = mp_apply_typed<T>(mp, IGA_OP_M, x, q, R, st, w))) return rc;
+    for (int r = 0; r < R; ++r) {
+        mp_init_kernel<T><<<grid, kMpThreads, 0, st>>>(b, q, w.res, z, p, dinv, G, r, w.partials);
+        IGA_LAUNCH_CHECK("mp_init_kernel");
+        mp_reduce_kernel<3><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
+        IGA_LAUNCH_CHECK("mp_reduce_kernel");
+    }
+    if ((rc = reduce_all())) return rc;
+    for (int r = 0; r < R; ++r) {
+        rr[r] = red[3 * r];
+        rz[r] = red[3 * r + 1];
+        bn[r] = std::sqrt(red[3 * r + 2]);
+        active[r] = bn[r] > 0.0 && !(rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]);
+        if (!(bn[r] > 0.0)) IGA_CUDA(cudaMemsetAsync(x + (size_t)r * G, 0, sizeof(T) * G, st));
+    }
+    for (int it = 0; it < max_it; ++it) {
+        bool any = false;
+        for (int r = 0; r < R; ++r) any = any || active[r];
+        if (!any) break;
+        if ((rc = mp_apply_typed<T>(mp, IGA_OP_M, p, q, R, st, w))) return rc;
+        for (int r = 0; r < R; ++r) {
+            if (!active[r]) continue;
+            mp_dot_kernel<T><<<grid, kMpThreads, 0, st>>>(p, q, G, r, w.partials);
+            IGA_LAUNCH_CHECK("mp_dot_kernel");
+            mp_reduce_kernel<1><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
+            IGA_LAUNCH_CHECK("mp_reduce_kernel");
+        }
+        if ((rc = reduce_all())) return rc;
+        std::vector<double> alpha(R, 0.0);
+        for (int r = 0; r < R; ++r) {
+            if (!active[r]) continue;
+            const double pq = red[3 * r];
+            if (!(pq > 0.0) || !std::isfinite(pq)) return fail(IGA_ERR_NONFINITE, "CG breakdown: (p, M p) <= 0 or non-finite");
+            alpha[r] = rz[r] / pq;
+            mp_update_kernel<T><<<grid, kMpThreads, 0, st>>>(x, w.res, z, p, q, dinv, G, r, alpha[r], w.partials);
+            IGA_LAUNCH_CHECK("mp_update_kernel");
+            mp_reduce_kernel<2><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
+            IGA_LAUNCH_CHECK("mp_reduce_kernel");
+        }
+        if ((rc = reduce_all())) return rc;
+        for (int r = 0; r < R; ++r) {
+            if (!active[r]) continue;
+            iters[r] += 1;
+            rr[r] = red[3 * r];
+            const double rz_new = red[3 * r + 1];
+            if (rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]) {
+                active[r] = 0;
+                continue;
+            }
+            const double beta = rz_new / rz[r];
+            rz[r] = rz_new;
+            mp_dir_kernel<T><<<grid, kMpThreads, 0, st>>>(p, z, G, r, beta);
+            IGA_LAUNCH_CHECK("mp_dir_kernel");
+        }
+    }
+    bool nc = false;
+    for (int r = 0; r < R; ++r) {
+        const double rel = bn[r] > 0.0 ? std::sqrt(rr[r]) / bn[r] : 0.0;
+        if (iters_out) iters_out[r] = iters[r];
+        if (relres_out) relres_out[r] = rel;
+        if (rtol > 0.0 && rel > rtol) nc = true;
+    }
+    IGA_CUDA(cudaStreamSynchronize(st));
+    if (nc) return fail(IGA_ERR_NOT_CONVERGED, "multi-patch CG reached max_it before rtol");
+    return IGA_OK;
+}
+
+}  // namespace
+}  // namespace iga
+
+extern "C" int iga_multipatch_apply(const iga_multipatch* mp, int which, int dtype, const void* x, void* y, int nrhs,
+                                    void* stream) {
+    if (!mp || !x || !y) return fail(IGA_ERR_ARG, "null argument");
+    if (which != IGA_OP_K && which != IGA_OP_M) return fail(IGA_ERR_ARG, "which must be IGA_OP_K or IGA_OP_M");
+    if (dtype != IGA_F32 && dtype != IGA_F64) return fail(IGA_ERR_ARG, "dtype must be IGA_F32 or IGA_F64");
+    if (nrhs < 0) return fail(IGA_ERR_ARG, "nrhs must be >= 0");
+    if (x == y) return fail(IGA_ERR_ARG, "y must not alias x");
+    if (nrhs == 0) return IGA_OK;
+    MpWork w;
+    const size_t es = dtype == IGA_F64 ? 8 : 4;
+    int rc = mp_work(mp, es, nrhs, w);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == IGA_F64 ? mp_apply_typed<double>(mp, which, (const double*)x, (double*)y, nrhs, st, w)
+                            : mp_apply_typed<float>(mp, which, (const float*)x, (float*)y, nrhs, st, w);
+}
+
+extern "C" int iga_multipatch_mass_solve(const iga_multipatch* mp, int dtype, const void* b, void* x, int nrhs,
+                                         double rtol, int max_it, int* iters_out, double* relres_out, void* stream) {
+    if (!mp || !b || !x) return fail(IGA_ERR_ARG, "null argument");
+    if (dtype != IGA_F32 && dtype != IGA_F64) return fail(IGA_ERR_ARG, "dtype must be IGA_F32 or IGA_F64");
+    if (nrhs < 0 || max_it < 0 || !(rtol >= 0.0)) return fail(IGA_ERR_ARG, "bad nrhs / max_it / rtol");
+    if (b == x) return fail(IGA_ERR_ARG, "x must not alias b");
+    if (nrhs == 0) return IGA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == IGA_F64
+               ? mp_solve_typed<double>(mp, (const double*)b, (double*)x, nrhs, rtol, max_it, iters_out, relres_out, st)
+               : mp_solve_typed<float>(mp, (const float*)b, (float*)x, nrhs, rtol, max_it, iters_out, relres_out, st);
+}

@@ -79,7 +79,13 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
     if (d.map_kind == IGA_MAP_ANNULUS_QUARTER && d.dim != 2)
         return fail(IGA_ERR_ARG, "ANNULUS_QUARTER map is 2-D");
     if (d.map_kind == IGA_MAP_CUBE_SINE && d.dim != 3) return fail(IGA_ERR_ARG, "CUBE_SINE map is 3-D");
-    if (d.map_kind < 0 || d.map_kind > 2) return fail(IGA_ERR_ARG, "unknown map_kind");
+    if (d.map_kind < 0 || d.map_kind > 3) return fail(IGA_ERR_ARG, "unknown map_kind");
+    if (d.map_kind == IGA_MAP_ANNULUS_SECTOR) {
+        if (d.dim != 2) return fail(IGA_ERR_ARG, "ANNULUS_SECTOR map is 2-D");
+        const double dr = d.sector[1] - d.sector[0], da = d.sector[3] - d.sector[2];
+        if (!(d.sector[0] > 0.0) || !(d.sector[1] > 0.0) || !(dr * da > 0.0))
+            return fail(IGA_ERR_ARG, "ANNULUS_SECTOR needs radii > 0 and (r1 - r0)(a1 - a0) > 0");
+    }
     if (d.coef_kind < 0 || d.coef_kind > 2) return fail(IGA_ERR_ARG, "unknown coef_kind");
     if (d.coef_kind == IGA_COEF_SINCOS && d.dim != 2) return fail(IGA_ERR_ARG, "SINCOS coefficient is 2-D");
     if (d.coef_kind == IGA_COEF_BSPLINE) {
@@ -166,6 +172,7 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
     gp.nq = nq;
     gp.map_kind = d.map_kind;
     gp.map_param = d.map_param;
+    for (int k = 0; k < 4; ++k) gp.sector[k] = d.sector[k];
     gp.coef_kind = d.coef_kind;
     gp.coef_param = d.coef_param;
     gp.theta = s->theta.as<double>();

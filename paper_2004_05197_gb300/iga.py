@@ -22,7 +22,7 @@ _lib = C.CDLL(LIB_PATH)
 IGA_OK = 0
 IGA_ERR_ARG, IGA_ERR_OOM, IGA_ERR_CUDA = -1, -2, -3
 IGA_ERR_NOT_CONVERGED, IGA_ERR_NONFINITE, IGA_ERR_TIMEOUT = -4, -5, -6
-IGA_MAP_IDENTITY, IGA_MAP_ANNULUS_QUARTER, IGA_MAP_CUBE_SINE = 0, 1, 2
+IGA_MAP_IDENTITY, IGA_MAP_ANNULUS_QUARTER, IGA_MAP_CUBE_SINE, IGA_MAP_ANNULUS_SECTOR = 0, 1, 2, 3
 IGA_COEF_CONST, IGA_COEF_SINCOS, IGA_COEF_BSPLINE = 0, 1, 2
 IGA_F32, IGA_F64 = 0, 1
 IGA_OP_K, IGA_OP_M = 0, 1
@@ -39,6 +39,8 @@ EXPORTED = [
     "iga_wave_set_timing", "iga_wave_stats_get", "iga_ops_spectrum", "iga_wave_adjoint",
     "iga_batch_create", "iga_batch_destroy", "iga_batch_step", "iga_batch_tune", "iga_batch_partition",
     "iga_mass_solve_noalloc", "iga_sampling_length_for_mesh",
+    "iga_multipatch_create", "iga_multipatch_destroy", "iga_multipatch_size", "iga_multipatch_global_index",
+    "iga_multipatch_apply", "iga_multipatch_mass_solve",
 ]
 
 
@@ -52,7 +54,7 @@ class iga_space_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("n_el", C.c_int), ("map_kind", C.c_int),
                 ("map_param", C.c_double), ("coef_kind", C.c_int), ("coef_param", C.c_double),
                 ("theta", C.POINTER(C.c_double)), ("n_theta", C.c_int), ("theta_degree", C.c_int),
-                ("quad_pts", C.c_int)]
+                ("quad_pts", C.c_int), ("sector", C.c_double * 4)]
 
 
 class iga_space_info(C.Structure):
@@ -67,6 +69,11 @@ class iga_ops_info(C.Structure):
                 ("D", C.c_int), ("ns", C.c_int), ("n_band_elements", C.c_int),
                 ("n_sample_rows", C.c_int), ("t_sample_ms", C.c_double), ("t_band_ms", C.c_double),
                 ("t_interp_ms", C.c_double), ("t_eval_ms", C.c_double), ("t_total_ms", C.c_double)]
+
+
+class iga_interface(C.Structure):
+    _fields_ = [("patch_a", C.c_int), ("side_a", C.c_int), ("patch_b", C.c_int), ("side_b", C.c_int),
+                ("reversed", C.c_int)]
 
 
 class iga_wave_desc(C.Structure):
@@ -98,6 +105,12 @@ _sig = {
     "iga_ops_sample_indices": [_vp, C.POINTER(_i)],
     "iga_stencil_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
     "iga_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
+    "iga_multipatch_create": [_i, C.POINTER(_vp), _i, C.POINTER(iga_interface), C.POINTER(_vp)],
+    "iga_multipatch_destroy": [_vp],
+    "iga_multipatch_size": [_vp, C.POINTER(C.c_longlong)],
+    "iga_multipatch_global_index": [_vp, _i, C.POINTER(C.c_longlong)],
+    "iga_multipatch_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
+    "iga_multipatch_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_sampling_length_for_mesh": [_d, _i, _i, _d, _d, _d, _d, C.POINTER(_i)],
     "iga_mass_solve_noalloc": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_wave_create": [_vp, C.POINTER(iga_wave_desc), C.POINTER(_vp)],
@@ -161,14 +174,15 @@ def _host_f64(a):
 
 # ---- space ---------------------------------------------------------------------
 def iga_space_create(dim, p, n_el, map_kind, map_param=0.0, coef_kind=IGA_COEF_CONST, coef_param=1.0,
-                     theta=None, n_theta=0, theta_degree=3, quad_pts=0):
-    """theta: host array, colex flat (first parametric direction fastest)."""
+                     theta=None, n_theta=0, theta_degree=3, quad_pts=0, sector=(0.0, 0.0, 0.0, 0.0)):
+    """theta: host array, colex flat (first parametric direction fastest);
+    sector: (r0, r1, a0, a1) of IGA_MAP_ANNULUS_SECTOR."""
     keep = None
     tptr = C.POINTER(C.c_double)()
     if theta is not None:
         keep, tptr = _host_f64(np.asarray(theta).ravel())
     desc = iga_space_desc(dim, p, n_el, map_kind, map_param, coef_kind, coef_param, tptr, n_theta,
-                          theta_degree, quad_pts)
+                          theta_degree, quad_pts, (C.c_double * 4)(*sector))
     out = C.c_void_p()
     _check(_lib.iga_space_create(C.byref(desc), C.byref(out)))
     del keep
@@ -254,6 +268,45 @@ def iga_mass_solve_noalloc(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_s
     if want_stats:
         return rc, np.array(iters[:]), np.array(rel[:])
     return rc, None, None
+
+
+# ---- multi-patch -----------------------------------------------------------------
+def iga_multipatch_create(patch_ops, interfaces):
+    """patch_ops: list of iga_ops handles; interfaces: (patch_a, side_a, patch_b, side_b, reversed)."""
+    arr = (C.c_void_p * len(patch_ops))(*[o.value if isinstance(o, C.c_void_p) else o for o in patch_ops])
+    ifs = (iga_interface * max(1, len(interfaces)))(*[iga_interface(*t) for t in interfaces])
+    out = C.c_void_p()
+    _check(_lib.iga_multipatch_create(len(patch_ops), arr, len(interfaces), ifs, C.byref(out)))
+    return out
+
+
+def iga_multipatch_destroy(mp):
+    _check(_lib.iga_multipatch_destroy(mp))
+
+
+def iga_multipatch_size(mp):
+    n = C.c_longlong()
+    _check(_lib.iga_multipatch_size(mp, C.byref(n)))
+    return int(n.value)
+
+
+def iga_multipatch_global_index(mp, patch, n_local):
+    out = np.zeros(n_local, dtype=np.int64)
+    _check(_lib.iga_multipatch_global_index(mp, patch, out.ctypes.data_as(C.POINTER(C.c_longlong))))
+    return out
+
+
+def iga_multipatch_apply(mp, which, dtype, x, y, nrhs, stream=None):
+    _check(_lib.iga_multipatch_apply(mp, which, dtype, _dptr(x), _dptr(y), nrhs, _stream(stream)))
+
+
+def iga_multipatch_mass_solve(mp, dtype, b, x, nrhs, rtol, max_it, stream=None, allow_not_converged=False):
+    iters = (C.c_int * nrhs)()
+    rel = (C.c_double * nrhs)()
+    ok = (IGA_OK, IGA_ERR_NOT_CONVERGED) if allow_not_converged else (IGA_OK,)
+    rc = _check(_lib.iga_multipatch_mass_solve(mp, dtype, _dptr(b), _dptr(x), nrhs, rtol, max_it, iters, rel,
+                                               _stream(stream)), ok)
+    return rc, np.array(iters[:]), np.array(rel[:])
 
 
 # ---- waves ---------------------------------------------------------------------
