@@ -59,6 +59,21 @@ def mesh_dependent_sampling_length(h, p, q, a=0.0, b=0.0, C=1.0, eps=0.1):
     return max(1, int(np.floor(C * h ** (eps - 1.0 + (p + a) / (q + b)))))
 
 
+def _true_rows_chunk(args):
+    space, rows = args
+    return true_rows(space, rows)
+
+
+def parallel_true_rows(space, rows, pool=None, chunks=64):
+    """true_rows() of many rows, optionally split into chunks over an executor's map();
+    rows are independent, so the result is the same as one call."""
+    if pool is None or len(rows) < 2 * chunks:
+        return true_rows(space, rows)
+    parts = np.array_split(np.asarray(rows), chunks)
+    out = list(pool.map(_true_rows_chunk, [(space, p) for p in parts]))
+    return np.concatenate([o[0] for o in out]), np.concatenate([o[1] for o in out])
+
+
 def interp_knots(xs, q):
     """Knot vector of order q+1 for interpolation at abscissae xs (de Boor averaging)."""
     xs = np.asarray(xs, dtype=np.float64)
@@ -70,7 +85,9 @@ def interp_knots(xs, q):
 class Surrogate:
     """Surrogate K~ and M~ of a Space for interpolation degree q and sampling length M."""
 
-    def __init__(self, space, q, M):
+    def __init__(self, space, q, M, pool=None):
+        """pool: optional executor whose map() runs the true-row quadrature of chunks of
+        the sample rows in parallel (the same arithmetic, row by row)."""
         self.space, self.q, self.M = space, q, M
         sp = space
         self.lo, self.hi = interior_range(sp.m, sp.p)
@@ -86,7 +103,7 @@ class Surrogate:
         # 3. sample values: true rows at every sample row (tensor grid of samples)
         grids = np.meshgrid(*([self.samp] * sp.dim), indexing='ij')
         srows = np.stack([g.ravel(order='F') for g in grids], axis=1)   # colex order
-        TK, TM = true_rows(sp, srows)
+        TK, TM = parallel_true_rows(sp, srows, pool)
         shape = (ns,) * sp.dim
         # samples[t] is a (ns,)*dim array indexed [s_1, .., s_d]
         self.sK = TK.T.reshape((sp.D,) + shape[::-1]).transpose([0] + list(range(sp.dim, 0, -1)))
