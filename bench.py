@@ -71,6 +71,21 @@ def pcg_profiled_traffic():
         return None
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (replicas: every rank times the same work on its GPU)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, ms_step, world):
+    """Whole-job throughput: the units all ranks processed divided by the slowest time."""
+    return world * units_per_rank / (ms_step / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
 
@@ -212,17 +227,13 @@ def run_ours(args, rank, world, device):
         # the library counts one launch per solve graph; it runs init 1, init 2, zero-RHS,
         # finish and two kernels per iteration
         launches += 3 * cg_solves + 2 * cg_it
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, device)
 
     oinfo = iga.iga_ops_info_get(ops)
     K = args.steps
     ms_step = ms / K
     shot_steps = args.nshot * nsteps
-    value = world * shot_steps / (ms_step / 1e3)
+    value = replica_value(shot_steps, ms_step, world)
     # dominant kernel: the persistent PCG launch (events around every launch, on its stream)
     init_b, it_b = cg_bytes(oinfo.nM, 1, 4)
     # one shot: every launch is one solve and the device counter holds its iterations
