@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         if (!grid_barrier(q.bar, err, nb)) return;
         // ---- CG init 1: r = b - M~a, cu = D^-1 r
         {
-            for (int k = 0; k < 3 * R; ++k) part[k] = 0.0;
+            DotAcc<float> dot[3 * R];
             const PlainLoadB<float> ld{q.a, q.ld};
             for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
                 float acc[R], own[R];
@@ -125,20 +125,22 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
                     stencil_row_interior<DIM, P, float, true, R, kBUnroll<R>>(q.FM, q.pitch, ld, i, sdlK, acc, own);
                 else
                     stencil_row<DIM, P, float, true, R, kBUnroll<R>>(q.FM, q.pitch, ld, i, q.N, q.m, acc, own);
-                const double di = (double)q.dinv[i];
+                const float di = q.dinv[i];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const long long o = (long long)r * q.ld + i;
-                    const double bi = (double)q.b[o];
-                    const double ri = bi - (double)acc[r];
-                    const float ui = (float)(di * ri);
+                    const float bi = q.b[o];
+                    const double ri = (double)bi - (double)acc[r];   // FP64 residual
+                    const float rt = (float)ri;
+                    const float ui = di * rt;
                     q.r[o] = ri;
                     q.cu[o] = ui;
-                    part[3 * r] += ri * (double)ui;
-                    part[3 * r + 1] += ri * ri;
-                    part[3 * r + 2] += bi * bi;
+                    dot[3 * r].add(rt, ui);
+                    dot[3 * r + 1].add(rt, rt);
+                    dot[3 * r + 2].add(bi, bi);
                 }
             }
+            for (int k = 0; k < 3 * R; ++k) part[k] = dot[k].value();
             block_sum<3 * R, kBWarps>(part, wsum, red);
             if (threadIdx.x < 3 * R) q.partials[(size_t)lb * S10 + 6 * R + threadIdx.x] = red[threadIdx.x];
             if (threadIdx.x < R) active[threadIdx.x] = 1;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         if (!grid_barrier(q.bar, err, nb)) return;
         // ---- phase 2 (init): cw = M~ cu
         auto phase2 = [&]() {
-            for (int k = 0; k < R; ++k) part[k] = 0.0;
+            DotAcc<float> dot[R];
             const PlainLoadB<float> ld{q.cu, q.ld};
             for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
                 float acc[R], own[R];
@@ -158,9 +160,10 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
                 for (int r = 0; r < R; ++r) {
                     if (!active[r]) continue;
                     q.cw[(long long)r * q.ld + i] = acc[r];
-                    part[r] += (double)own[r] * (double)acc[r];
+                    dot[r].add(own[r], acc[r]);
                 }
             }
+            for (int k = 0; k < R; ++k) part[k] = dot[k].value();
             block_sum<R, kBWarps>(part, wsum, red);
             if (threadIdx.x < R) q.partials[(size_t)lb * S10 + 4 * R + threadIdx.x] = red[threadIdx.x];
         };
@@ -193,9 +196,9 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
             for (int r = 0; r < R; ++r) any = any || active[r];
             if (!any) break;
             const int off1 = (it & 1) * 2 * R;
-            for (int k = 0; k < 2 * R; ++k) part[k] = 0.0;
+            DotAcc<float> dot[2 * R];
             for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
-                const double di = (double)q.dinv[i];
+                const float di = q.dinv[i];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if (!active[r]) continue;
@@ -206,14 +209,16 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
                     q.cp[o] = pi;
                     q.cs[o] = si;
                     q.a[o] = q.a[o] + al * pi;
-                    const double ri = q.r[o] - alpha[r] * (double)si;
-                    const float ui = (float)(di * ri);
+                    const double ri = q.r[o] - alpha[r] * (double)si;   // FP64 residual
+                    const float rt = (float)ri;
+                    const float ui = di * rt;
                     q.r[o] = ri;
                     q.cu[o] = ui;
-                    part[2 * r] += ri * (double)ui;
-                    part[2 * r + 1] += ri * ri;
+                    dot[2 * r].add(rt, ui);
+                    dot[2 * r + 1].add(rt, rt);
                 }
             }
+            for (int k = 0; k < 2 * R; ++k) part[k] = dot[k].value();
             block_sum<2 * R, kBWarps>(part, wsum, red);
             if (threadIdx.x < 2 * R) q.partials[(size_t)lb * S10 + off1 + threadIdx.x] = red[threadIdx.x];
             if (!grid_barrier(q.bar, err, nb)) return;

@@ -81,6 +81,36 @@ __device__ __host__ inline void cg_scalars(double gamma_new, double rr, double d
     gamma = gamma_new;
 }
 
+// Per-thread dot-product accumulator.  FP64 path: plain FP64 products and sums.
+// FP32 path: each product of two FP32 numbers is split exactly into p + e
+// (TwoProd through fmaf) and added to an unevaluated pair hi + lo with Knuth's
+// TwoSum, so a thread's partial sum carries about 48 significant bits while
+// using FP32 instructions only; the pair is widened to FP64 for the block and
+// grid reductions.  (On this part the FP64 pipe issues about 1.6 DFMA per clock
+// and SM against about 117 FFMA: per-row FP64 products cost more time than the
+// row's memory traffic.)  The explicit _rn intrinsics keep the compiler from
+// contracting the TwoSum steps into FMAs.
+template <typename T>
+struct DotAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s += a * b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Coherent loads of vectors written inside the same persistent launch.
 template <typename T>
 struct PlainLoadB {

@@ -6,8 +6,11 @@
 // the same iterates as the textbook recurrence in exact arithmetic.  Each
 // iteration is two grid-wide phases: a vector update (phase 1) and the mass
 // apply with its dot product (phase 2).
-// FP32 dtype: fields and the vectors u, w, p, s, x in FP32; the residual r and
-// every dot product in FP64.  Dot products are reduced deterministically:
+// FP32 dtype: fields and the vectors u, w, p, s, x in FP32; the residual r in
+// FP64 (one FP64 FMA per row and iteration).  Dot products: exact FP32 products
+// summed per thread in a compensated FP32 pair (DotAcc, about 48 significant
+// bits), then in FP64 across threads and blocks; u = D^-1 r is formed in FP32
+// from r rounded to FP32.  Dot products are reduced deterministically:
 // per-block partials, then a fixed-order warp reduction that every block
 // performs identically.
 //
@@ -128,35 +131,37 @@ __device__ __forceinline__ void mass_apply_row(const CgVecs<T>& v, const Load& l
 // init 1: r = b - M~x, u = D^-1 r; partials (r,u), (r,r), (b,b)
 template <int DIM, int P, typename T, int R>
 __device__ __forceinline__ void cg_init1(const CgVecs<T>& v, double* part, const int* sdl) {
-    for (int k = 0; k < 3 * R; ++k) part[k] = 0.0;
+    DotAcc<T> dot[3 * R];
     PlainLoad<T> ld{v.x, v.ldu, v.ext_user};
     const int dmax = max_delta<DIM, P>(v.m);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
         mass_apply_row<DIM, P, T, R>(v, ld, i, dmax, sdl, acc, own);
-        const double di = IGA_IN(i, v.ext_diag, 6) ? (double)v.dinv[i] : 0.0;
+        const T di = IGA_IN(i, v.ext_diag, 6) ? v.dinv[i] : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const long long ou = (long long)r * v.ldu + i, ow = (long long)r * v.ldw + i;
             const bool ok = IGA_IN(ou, v.ext_user, 7) && IGA_IN(ow, v.ext_vec, 16);
-            const double bi = ok ? (double)v.b[ou] : 0.0;
-            const double ri = bi - (double)acc[r];
-            const T ui = (T)(di * ri);
+            const T bi = ok ? v.b[ou] : T(0);
+            const double ri = (double)bi - (double)acc[r];   // FP64 residual
+            const T rt = (T)ri;
+            const T ui = di * rt;
             if (ok) {
                 v.r[ow] = ri;
                 v.u[ow] = ui;
             }
-            part[3 * r + 0] += ri * (double)ui;
-            part[3 * r + 1] += ri * ri;
-            part[3 * r + 2] += bi * bi;
+            dot[3 * r + 0].add(rt, ui);
+            dot[3 * r + 1].add(rt, rt);
+            dot[3 * r + 2].add(bi, bi);
         }
     }
+    for (int k = 0; k < 3 * R; ++k) part[k] = dot[k].value();
 }
 
 // phase 2 (and init 2): w = M~u; partial (w,u)
 template <int DIM, int P, typename T, int R>
 __device__ __forceinline__ void cg_phase2(const CgVecs<T>& v, const int* active, double* part, const int* sdl) {
-    for (int k = 0; k < R; ++k) part[k] = 0.0;
+    DotAcc<T> dot[R];
     PlainLoad<T> ld{v.u, v.ldw, v.ext_vec};
     const int dmax = max_delta<DIM, P>(v.m);
     // Full grid-stride rounds one row per thread; for a single right-hand side a
@@ -175,7 +180,7 @@ __device__ __forceinline__ void cg_phase2(const CgVecs<T>& v, const int* active,
             if (!active[r]) continue;
             const long long o = (long long)r * v.ldw + i;
             if (IGA_IN(o, v.ext_vec, 8)) v.w[o] = acc[r];
-            part[r] += (double)own[r] * (double)acc[r];
+            dot[r].add(own[r], acc[r]);
         }
     }
     const int lane = threadIdx.x & 31;
@@ -188,10 +193,11 @@ __device__ __forceinline__ void cg_phase2(const CgVecs<T>& v, const int* active,
                 if (!active[r]) continue;
                 const long long o = (long long)r * v.ldw + i;
                 if (IGA_IN(o, v.ext_vec, 8)) v.w[o] = acc[r];
-                part[r] += (double)own[r] * (double)acc[r];
+                dot[r].add(own[r], acc[r]);
             }
         }
     }
+    for (int k = 0; k < R; ++k) part[k] = dot[k].value();
 }
 
 // phase 1: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r;
@@ -200,9 +206,9 @@ __device__ __forceinline__ void cg_phase2(const CgVecs<T>& v, const int* active,
 template <typename T, int R>
 __device__ __forceinline__ void cg_phase1(const CgVecs<T>& v, const double* alpha, const double* beta,
                                           const int* active, double* part) {
-    for (int k = 0; k < 2 * R; ++k) part[k] = 0.0;
+    DotAcc<T> dot[2 * R];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.N; i += gridDim.x * blockDim.x) {
-        const double di = IGA_IN(i, v.ext_diag, 9) ? (double)v.dinv[i] : 0.0;
+        const T di = IGA_IN(i, v.ext_diag, 9) ? v.dinv[i] : T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!active[r]) continue;
@@ -215,14 +221,16 @@ __device__ __forceinline__ void cg_phase1(const CgVecs<T>& v, const double* alph
             v.p[o] = pi;
             v.s[o] = si;
             v.x[ou] = v.x[ou] + al * pi;
-            const double ri = v.r[o] - alpha[r] * (double)si;
-            const T ui = (T)(di * ri);
+            const double ri = v.r[o] - alpha[r] * (double)si;   // FP64 residual
+            const T rt = (T)ri;
+            const T ui = di * rt;
             v.r[o] = ri;
             v.u[o] = ui;
-            part[2 * r + 0] += ri * (double)ui;
-            part[2 * r + 1] += ri * ri;
+            dot[2 * r + 0].add(rt, ui);
+            dot[2 * r + 1].add(rt, rt);
         }
     }
+    for (int k = 0; k < 2 * R; ++k) part[k] = dot[k].value();
 }
 
 struct CgCtl {

@@ -218,6 +218,29 @@ def test_mass_solve_iterates_match_oracle_pcg(schedule):
     assert np.abs(xg.cpu().numpy()[0] - xr).max() <= 1e-11 * np.abs(xr).max()
 
 
+@pytest.mark.parametrize("name", ["annulus40_p3_sincos", "cube20_p2_theta_M2"])
+@pytest.mark.parametrize("schedule", list(SCHEDULES))
+def test_mass_solve_fp32_iterates_match_oracle_pcg(name, schedule):
+    """FP32 path (FP32 fields and vectors, FP64 residual, compensated FP32 dot products
+    widened to FP64 across threads), fixed 25 iterations, against the FP64 oracle PCG on
+    the same FP32-rounded operator and inputs: what is left is the FP32 rounding of the
+    CG vectors, checked at the FP32 tolerance 2e-5 of the largest iterate entry."""
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    M = stencil_to_csr(sp, SM)
+    dinv = (1.0 / M.diagonal()).astype(np.float32).astype(np.float64)
+    M.data = M.data.astype(np.float32).astype(np.float64)
+    b = inputs.vectors(sp.N, 1)[0].astype(np.float32)
+    x0 = (0.1 * inputs.vectors(sp.N, 1, seed=99)[0]).astype(np.float32)
+    xr, it, _ = pcg(M, b.astype(np.float64), x0.astype(np.float64), dinv, 0.0, 25)
+    bg = torch.tensor(b[None], device="cuda")
+    xg = torch.tensor(x0[None], device="cuda")
+    rc, iters, _ = iga.iga_mass_solve(ops, iga.IGA_F32, bg, xg, 1, 0.0, 25, flags=SCHEDULES[schedule])
+    assert iters[0] == 25 and it == 25
+    err = np.abs(xg.cpu().numpy()[0].astype(np.float64) - xr).max() / np.abs(xr).max()
+    assert err <= 2e-5, err
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_mass_solve_plain_and_persistent_schedules_agree_bitwise(dtype):
     _, ops = gpu_ops("cube20_p2_theta")
