@@ -178,7 +178,8 @@ def run_ours(args, rank, world, device):
     sflags = iga.IGA_SOLVE_GRAPH if args.solve == "graph" else 0
     wave = iga.iga_wave_create(ops, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
                                f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
-                               cg_max_it=args.cg_max_it, cfl_check=2, solve_flags=sflags)
+                               cg_max_it=args.cg_max_it, cfl_check=2, solve_flags=sflags,
+                               cg_guess=args.cg_guess)
     iga.iga_wave_set_timing(wave, True)
 
     def one_pass(old_ops):
@@ -267,6 +268,8 @@ def run_ours(args, rank, world, device):
         "config": {"workload": args.workload, "dim": w["dim"], "p": w["p"], "n_el": w["n_el"], "N": N,
                    "q": w["q"], "M": w["M"], "nsteps": nsteps, "nshot": args.nshot, "cg_rtol": args.cg_rtol,
                    "cg_schedule": args.solve,
+                   "cg_start": ["previous acceleration", "linear extrapolation in time",
+                                "quadratic extrapolation in time"][args.cg_guess],
                    "precision": "FP32 fields/vectors/apply, FP64 quadrature, residual and dot products",
                    "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (
                        (oinfo.nK + oinfo.nM) * oinfo.pitch * 12 / 1e9),
@@ -298,7 +301,8 @@ def fp64_plain_and_error(ctx, args):
     N = iga.iga_ops_info_get(ops).N
     res = {}
     w64 = iga.iga_wave_create(ops, 1, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1,
-                              cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN)
+                              cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN,
+                              cg_guess=args.cg_guess)
     torch.cuda.synchronize()
     t = time.perf_counter()
     iga.iga_wave_step(w64, P)
@@ -309,7 +313,7 @@ def fp64_plain_and_error(ctx, args):
     u64 = torch.empty((1, N), dtype=torch.float64, device="cuda")
     iga.iga_wave_get_state(w64, u64)
     w32 = iga.iga_wave_create(ops, 1, iga.IGA_F32, dt, src_pos=src, f0=10.0, t0=0.1,
-                              cg_rtol=args.cg_rtol, cg_max_it=args.cg_max_it)
+                              cg_rtol=args.cg_rtol, cg_max_it=args.cg_max_it, cg_guess=args.cg_guess)
     torch.cuda.synchronize()
     t = time.perf_counter()
     iga.iga_wave_step(w32, P)
@@ -348,7 +352,7 @@ def run_e2e(args, ctx):
         o = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
         wv = iga.iga_wave_create(o, args.nshot, iga.IGA_F32, dt, src_pos=np.repeat(src, args.nshot, 0),
                                  f0=10.0, t0=0.1, rec_pos=rec, nsteps_max=nsteps, cg_rtol=args.cg_rtol,
-                                 cg_max_it=args.cg_max_it,
+                                 cg_max_it=args.cg_max_it, cg_guess=args.cg_guess,
                                  solve_flags=iga.IGA_SOLVE_GRAPH if args.solve == "graph" else 0)
         iga.iga_wave_step(wv, nsteps)
         tr = iga.iga_wave_traces(wv, args.nshot, len(rec), nsteps)   # device -> host
@@ -642,6 +646,8 @@ def main():
     ap.add_argument("--nshot", type=int, default=1)
     ap.add_argument("--cg-rtol", type=float, default=1e-6)
     ap.add_argument("--cg-max-it", type=int, default=2000)
+    ap.add_argument("--cg-guess", type=int, default=2, choices=[0, 1, 2],
+                    help="CG start of each step: a^{n-1} (0), linear (1) or quadratic (2) extrapolation")
     ap.add_argument("--solve", default="persistent", choices=["persistent", "graph"],
                     help="CG schedule of the FP32 waves")
     ap.add_argument("--compare-steps", type=int, default=50)

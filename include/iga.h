@@ -271,6 +271,13 @@ typedef struct iga_wave_desc {
     int cfl_check;              /* 1: estimate lambda_max(M~^-1 K~) by Lanczos at create and at every
                                    reset; 2: at create only; 0: off.  With an estimate, steps
                                    with dt sqrt(lambda_max) >= 2 are refused (IGA_ERR_ARG) */
+    int cg_guess;               /* initial guess of step n's mass solve: 0 = a^{n-1};
+                                   1 = 2 a^{n-1} - a^{n-2} (linear extrapolation in time);
+                                   2 = 3 a^{n-1} - 3 a^{n-2} + a^{n-3} (quadratic).  The order
+                                   drops to what the steps done so far allow (a^{-1} = 0 at n = 0,
+                                   order 0 at n = 1, at most order 1 at n = 2).  Only the
+                                   starting point of the CG changes; every solve still runs to
+                                   cg_rtol.  wave_adjoint runs its forward sweeps with order 0 */
 } iga_wave_desc;
 
 int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);

@@ -75,11 +75,29 @@ def gaussian_pulse(space, xc, width):
     return np.exp(-np.sum((x - np.asarray(xc)) ** 2, axis=-1) / (2.0 * width ** 2))
 
 
+def cg_start(hist, order, n):
+    """Start of step n's mass solve from the accelerations of the earlier steps,
+    hist = [a^{n-1}, a^{n-2}, a^{n-3}] (as many as exist): zero before the first
+    step, else the polynomial extrapolation in time of degree min(order, len - 1)
+    through the last points (degree 0: a^{n-1}; 1: 2a^{n-1} - a^{n-2};
+    2: 3a^{n-1} - 3a^{n-2} + a^{n-3}).  The starting point is not part of the
+    time-stepping scheme: every solve still runs to its tolerance."""
+    if not hist:
+        return np.zeros(n)
+    k = min(order, len(hist) - 1)
+    if k == 0:
+        return hist[0].copy()
+    if k == 1:
+        return 2.0 * hist[0] - hist[1]
+    return 3.0 * (hist[0] - hist[1]) + hist[2]
+
+
 class Leapfrog:
     """Leapfrog on the (surrogate) stencil matrices SK, SM given for all rows."""
 
-    def __init__(self, space, SK, SM, dt, rtol=1e-10, max_it=1000):
+    def __init__(self, space, SK, SM, dt, rtol=1e-10, max_it=1000, guess_order=0):
         self.space = space
+        self.guess_order = guess_order
         self.K = stencil_to_csr(space, SK)
         self.M = stencil_to_csr(space, SM)
         self.dinv = 1.0 / self.M.diagonal()
@@ -97,7 +115,7 @@ class Leapfrog:
         rvec = np.array([point_values(sp, s) for s in receivers]).reshape(len(receivers), sp.N)
         u = np.asarray(u0, dtype=np.float64).copy()
         v = np.zeros_like(u) if v0 is None else np.asarray(v0, dtype=np.float64)
-        a_prev = np.zeros_like(u)
+        hist = []                   # a^{n-1}, a^{n-2}, a^{n-3} (most recent first)
         u_prev = None
         traces = np.zeros((len(receivers), nsteps))
         for n in range(nsteps):
@@ -106,14 +124,14 @@ class Leapfrog:
             for bvec, f0, t0, amp in svec:
                 f += amp * ricker(t, f0, t0) * bvec
             b = f - self.K @ u
-            a, it, _ = pcg(self.M, b, a_prev, self.dinv, self.rtol, self.max_it)
+            a, it, _ = pcg(self.M, b, cg_start(hist, self.guess_order, sp.N), self.dinv, self.rtol, self.max_it)
             self.iters.append(it)
             if n == 0:
                 u_new = u + dt * v + 0.5 * dt * dt * a
             else:
                 u_new = 2.0 * u - u_prev + dt * dt * a
             u_prev, u = u, u_new
-            a_prev = a
+            hist = [a] + hist[:2]
             if len(receivers):
                 traces[:, n] = rvec @ u
         return u, u_prev, traces

@@ -503,6 +503,15 @@ extern "C" int iga_wave_adjoint(iga_wave* w, int nsteps, int checkpoint_every, c
         return fail(IGA_ERR_ARG, "the gradient is taken with respect to a B-spline wave speed");
     cudaStream_t st = (cudaStream_t)stream;
     const int d = sp->dim, p = sp->p;
+    // The forward and the recomputed segments start every solve from a^{n-1}
+    // (cg_guess 0), so a checkpoint (u^n, u^{n-1}, a^{n-1}) restarts a segment
+    // exactly; the wave's own setting is restored on return.
+    struct GuessOff {
+        iga_wave* w;
+        int saved;
+        ~GuessOff() { w->desc.cg_guess = saved; }
+    } guess_off{w, w->desc.cg_guess};
+    w->desc.cg_guess = 0;
     int rc;
     if (d == 2 && p == 1) rc = adjoint_dp<2, 1>(w, nsteps, checkpoint_every, obs, J_out, grad_theta, st);
     else if (d == 2 && p == 2) rc = adjoint_dp<2, 2>(w, nsteps, checkpoint_every, obs, J_out, grad_theta, st);

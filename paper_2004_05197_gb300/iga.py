@@ -83,7 +83,7 @@ class iga_wave_desc(C.Structure):
                 ("src_pos", C.POINTER(C.c_double)), ("f0", C.c_double), ("t0", C.c_double),
                 ("src_amp", C.c_double), ("nrec", C.c_int), ("rec_pos", C.POINTER(C.c_double)),
                 ("nsteps_max", C.c_int), ("cg_rtol", C.c_double), ("cg_max_it", C.c_int),
-                ("cfl_check", C.c_int)]
+                ("cfl_check", C.c_int), ("cg_guess", C.c_int)]
 
 
 class iga_wave_stats(C.Structure):
@@ -312,7 +312,7 @@ def iga_multipatch_mass_solve(mp, dtype, b, x, nrhs, rtol, max_it, stream=None, 
 # ---- waves ---------------------------------------------------------------------
 def iga_wave_create(ops, nshot, dtype, dt, init_kind=IGA_INIT_ZERO, pulse_centre=None, pulse_width=0.05,
                     src_pos=None, f0=10.0, t0=0.1, src_amp=1.0, rec_pos=None, nsteps_max=0,
-                    cg_rtol=1e-10, cg_max_it=1000, solve_flags=0, cfl_check=1):
+                    cg_rtol=1e-10, cg_max_it=1000, solve_flags=0, cfl_check=1, cg_guess=0):
     keep = []
 
     def hp(a):
@@ -325,7 +325,7 @@ def iga_wave_create(ops, nshot, dtype, dt, init_kind=IGA_INIT_ZERO, pulse_centre
     nrec = 0 if rec_pos is None else int(np.asarray(rec_pos).shape[0])
     desc = iga_wave_desc(nshot, dtype, solve_flags, dt, init_kind, hp(pulse_centre), pulse_width,
                          1 if src_pos is not None else 0, hp(src_pos), f0, t0, src_amp, nrec,
-                         hp(rec_pos), nsteps_max, cg_rtol, cg_max_it, cfl_check)
+                         hp(rec_pos), nsteps_max, cg_rtol, cg_max_it, cfl_check, cg_guess)
     out = C.c_void_p()
     _check(_lib.iga_wave_create(ops, C.byref(desc), C.byref(out)))
     return out

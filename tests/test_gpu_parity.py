@@ -340,7 +340,8 @@ def test_wave_fp32_error_against_fp64_oracle():
     assert err <= 1e-5
 
 
-@pytest.mark.parametrize("mode", ["f64", "f64_plain", "f64_graph", "f32", "f32_graph"])
+@pytest.mark.parametrize("mode", ["f64", "f64_plain", "f64_graph", "f32", "f32_graph", "f64_guess2", "f32_guess2",
+                                  "f64_guess1"])
 def test_wave_cube_ricker_source_matches_oracle(mode):
     """3-D, lognormal wave speed, Ricker point source at the centre (the bench workload family)."""
     name = "cube20_p2_theta_M2"
@@ -355,9 +356,10 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     dtype = iga.IGA_F32 if f32 else iga.IGA_F64
     flags = {"f64_plain": iga.IGA_SOLVE_PLAIN, "f64_graph": iga.IGA_SOLVE_GRAPH,
              "f32_graph": iga.IGA_SOLVE_GRAPH}.get(mode, 0)
+    guess = int(mode[-1]) if "guess" in mode else 0
     wave = iga.iga_wave_create(ops, 1, dtype, dt, src_pos=src[None], f0=10.0, t0=0.1, rec_pos=rec,
                                nsteps_max=nsteps, cg_rtol=1e-6 if f32 else 1e-13,
-                               cg_max_it=3000, solve_flags=flags)
+                               cg_max_it=3000, solve_flags=flags, cg_guess=guess)
     iga.iga_wave_step(wave, nsteps)
     tdt = torch.float32 if f32 else torch.float64
     u = torch.empty((1, sp.N), dtype=tdt, device="cuda")
@@ -365,7 +367,7 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     torch.cuda.synchronize()
     tr = iga.iga_wave_traces(wave, 1, len(rec), nsteps)[0]
     iga.iga_wave_destroy(wave)
-    lf = Leapfrog(sp, SK, SM, dt, rtol=1e-13, max_it=3000)
+    lf = Leapfrog(sp, SK, SM, dt, rtol=1e-13, max_it=3000, guess_order=guess)
     ur, _, trr = lf.run(np.zeros(sp.N), nsteps, sources=[(src, 10.0, 0.1, 1.0)], receivers=list(rec))
     ug = u.cpu().numpy()[0].astype(np.float64)
     err = np.linalg.norm(ug - ur) / np.linalg.norm(ur)

@@ -379,3 +379,38 @@ def test_leapfrog_eigenmode_closed_form():
     u, _, _ = lf.run(v, n)
     w = np.arccos(1.0 - 0.5 * dt * dt * lam[k])
     np.testing.assert_allclose(u, np.cos(n * w) * v, atol=1e-9 * np.abs(v).max())
+
+
+def test_cg_start_reproduces_polynomials_in_time():
+    """The extrapolated CG start is exact on accelerations a^n that are polynomials in
+    n of the extrapolation degree, and the degree drops to what the history allows."""
+    from oracle.wave import cg_start
+    rng = np.random.default_rng(7)
+    c0, c1, c2 = rng.standard_normal((3, 11))
+    a = lambda n: c0 + c1 * n + c2 * n * n
+    n = 9
+    hist = [a(n - 1), a(n - 2), a(n - 3)]
+    np.testing.assert_allclose(cg_start(hist, 2, 11), a(n), rtol=0, atol=1e-12 * np.abs(a(n)).max())
+    lin = lambda n: c0 + c1 * n
+    np.testing.assert_allclose(cg_start([lin(n - 1), lin(n - 2), lin(n - 3)], 1, 11), lin(n), atol=1e-13)
+    # a quadratic is not reproduced by the linear rule (the c2 term is missed by 2 c2)
+    assert np.abs(cg_start(hist, 1, 11) - a(n)).max() > 0.1 * np.abs(c2).max()
+    assert np.array_equal(cg_start([], 2, 11), np.zeros(11))
+    assert np.array_equal(cg_start(hist[:1], 2, 11), hist[0])
+    np.testing.assert_allclose(cg_start(hist[:2], 2, 11), 2 * hist[0] - hist[1])
+
+
+def test_leapfrog_extrapolated_start_same_solution_fewer_iterations():
+    """The CG start changes the work, not the solution: at a tight tolerance the states
+    of guess orders 0 and 2 agree; at a loose one order 2 needs fewer iterations."""
+    sp, SK, SM = _small_wave()
+    dt = 0.2 / sp.n_el
+    u0 = gaussian_pulse(sp, AnnulusQuarter()(inputs.pulse_centre())[0], 0.15)
+    ua, _, _ = Leapfrog(sp, SK, SM, dt, rtol=1e-14, max_it=2000, guess_order=0).run(u0, 30)
+    ub, _, _ = Leapfrog(sp, SK, SM, dt, rtol=1e-14, max_it=2000, guess_order=2).run(u0, 30)
+    assert np.linalg.norm(ua - ub) <= 1e-12 * np.linalg.norm(ua)
+    l0 = Leapfrog(sp, SK, SM, dt, rtol=1e-8, max_it=2000, guess_order=0)
+    l2 = Leapfrog(sp, SK, SM, dt, rtol=1e-8, max_it=2000, guess_order=2)
+    l0.run(u0, 30)
+    l2.run(u0, 30)
+    assert sum(l2.iters) < sum(l0.iters)
