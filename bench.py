@@ -402,7 +402,8 @@ def run_batched(args):
         for g in range(2):
             waves.append(iga.iga_wave_create(ops, 8, iga.IGA_F32, W.dt_of(w), src_pos=src[8 * g:8 * g + 8],
                                              f0=10.0, t0=0.1, rec_pos=np.array([[0.5, 0.5]]), nsteps_max=nsteps + 64,
-                                             cg_rtol=args.batched_rtol, cg_max_it=args.cg_max_it, cfl_check=2))
+                                             cg_rtol=args.batched_rtol, cg_max_it=args.cg_max_it, cfl_check=2,
+                                             cg_guess=args.cg_guess))
     b = iga.iga_batch_create(waves)
     iga.iga_batch_tune(b, trial_steps=5, rounds=3)
     part = iga.iga_batch_partition(b, len(waves))
@@ -436,7 +437,7 @@ def run_batched(args):
     for k, (w, sp, ops, src) in enumerate(meshes):
         wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
                                  cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN,
-                                 cfl_check=0)
+                                 cfl_check=0, cg_guess=args.cg_guess)
         torch.cuda.synchronize()
         t = time.perf_counter()
         iga.iga_wave_step(wv, args.plain_steps)
@@ -445,7 +446,7 @@ def run_batched(args):
         plain_ss += args.plain_steps
         iga.iga_wave_destroy(wv)
         wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
-                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, cfl_check=0)
+                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, cfl_check=0, cg_guess=args.cg_guess)
         iga.iga_wave_step(wv, nsteps)
         N = iga.iga_ops_info_get(ops).N
         u = torch.empty((1, N), dtype=torch.float64, device="cuda")

@@ -11,7 +11,9 @@
 //   Jacobi-PCG, Chronopoulos-Gear form, all shots of the problem at once
 //   update          u^{n+1} = 2u^n - u^{n-1} + dt^2 a^n  (n = 0: u^0 + dt^2/2 a^0) into U[(n+1) mod 2]
 //   barrier, receivers of u^{n+1}
-// FP32 fields and state, FP64 residual and reductions (as mass_solve).
+// FP32 fields and state, FP64 residual and reductions (as mass_solve).  The CG
+// start of step n follows the wave's cg_guess (a^{n-1}, or its linear / quadratic
+// extrapolation in time from the accelerations in A[(n-1..n-3) % 3]).
 // The step counter lives in device memory, so one captured graph of the launch
 // can be replayed for consecutive step ranges.
 #include <algorithm>
@@ -40,7 +42,8 @@ struct BatchProb {
     int N, m;
     float* U[2];        // u^n in U[n % 2]
     float* L[2];        // low parts of the compensated state, alongside U
-    float* a;           // CG solution / next initial guess
+    float* A[3];        // CG solutions: a^n in A[n % 3] (one buffer three times when guess = 0)
+    int guess;          // CG start order (the wave's cg_guess): 0 = a^{n-1} in place
     float* b;           // right-hand side
     double* r;          // CG residual (FP64)
     float* cu;          // D^-1 r
@@ -100,6 +103,21 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         float* nxt = q.U[(n + 1) & 1];   // holds u^{n-1}; receives u^{n+1}
         const float* curlo = q.L[n & 1];
         float* nxtlo = q.L[(n + 1) & 1];
+        float* const qa = q.A[n % 3];   // receives a^n; holds the CG start
+        // ---- CG start extrapolated in time into A[n % 3] (which held a^{n-3}); the
+        // force phase's barrier orders it before the mass apply of CG init 1
+        if (q.guess > 0 && n >= 1) {
+            const int order = min(q.guess, n - 1);
+            const float* h0 = q.A[(n + 2) % 3];   // a^{n-1}
+            const float* h1 = q.A[(n + 1) % 3];   // a^{n-2}
+            for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const long long o = (long long)r * q.ld + i;
+                    const float a0 = h0[o];
+                    qa[o] = order == 0 ? a0 : order == 1 ? 2.f * a0 - h1[o] : 3.f * (a0 - h1[o]) + qa[o];
+                }
+        }
         // ---- force + source
         {
             const float amp = (float)(q.amp * ricker_dev(n * q.dt, q.f0, q.t0));
@@ -118,7 +136,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         // ---- CG init 1: r = b - M~a, cu = D^-1 r
         {
             DotAcc<float> dot[3 * R];
-            const PlainLoadB<float> ld{q.a, q.ld};
+            const PlainLoadB<float> ld{qa, q.ld};
             for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
                 float acc[R], own[R];
                 if (i >= dmax && i < q.N - dmax)
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         __syncthreads();
         for (int r = 0; r < R; ++r)
             if (!(bnorm[r] > 0.0))
-                for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) q.a[(long long)r * q.ld + i] = 0.f;
+                for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) qa[(long long)r * q.ld + i] = 0.f;
         // ---- CG iterations
         for (int it = 0; it < q.max_it; ++it) {
             bool any = false;
@@ -208,7 +226,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
                     const float si = q.cw[o] + be * q.cs[o];
                     q.cp[o] = pi;
                     q.cs[o] = si;
-                    q.a[o] = q.a[o] + al * pi;
+                    qa[o] = qa[o] + al * pi;
                     const double ri = q.r[o] - alpha[r] * (double)si;   // FP64 residual
                     const float rt = (float)ri;
                     const float ui = di * rt;
@@ -253,7 +271,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
                 for (int r = 0; r < R; ++r) {
                     const long long o = (long long)r * q.ld + i;
                     float hn, ln;
-                    leapfrog_comp(cur[o], curlo[o], nxt[o], nxtlo[o], __fmul_rn(n == 0 ? 0.5f * dt2 : dt2, q.a[o]),
+                    leapfrog_comp(cur[o], curlo[o], nxt[o], nxtlo[o], __fmul_rn(n == 0 ? 0.5f * dt2 : dt2, qa[o]),
                                   n == 0, hn, ln);
                     nxt[o] = hn;
                     nxtlo[o] = ln;
@@ -375,13 +393,46 @@ static int upload_probs(iga_batch* b, cudaStream_t st) {
 // then 2 clocks per problem
 static int* batch_err(iga_batch* b) { return (int*)b->counters.as<long long>(); }
 
-// Bind U[n % 2] to the waves' current buffers and load the step counters (a wave
-// may have been reset or stepped on its own since the last launch).
+static int mod3(int n) { return ((n % 3) + 3) % 3; }
+
+// The wave keeps a^{step-1}, a^{step-2}, a^{step-3} in a, ah1, ah2 (cg_guess > 0);
+// the kernel finds a^n in A[n % 3].
+static void accel_buffers(const iga_wave* w, float* A[3]) {
+    if (w->desc.cg_guess > 0) {
+        A[mod3(w->step - 1)] = w->a.as<float>();
+        A[mod3(w->step - 2)] = w->ah1.as<float>();
+        A[mod3(w->step - 3)] = w->ah2.as<float>();
+    } else {
+        A[0] = A[1] = A[2] = w->a.as<float>();
+    }
+}
+
+// After steps ran in the kernel: the wave's u / uprev / a views for its new step.
+static void wave_views(iga_wave* w, const BatchProb& q) {
+    w->u.ptr = q.U[w->step & 1];
+    w->uprev.ptr = q.U[(w->step + 1) & 1];
+    w->ulo.ptr = q.L[w->step & 1];
+    w->uprevlo.ptr = q.L[(w->step + 1) & 1];
+    if (w->desc.cg_guess > 0) {
+        w->a.ptr = q.A[mod3(w->step - 1)];
+        w->ah1.ptr = q.A[mod3(w->step - 2)];
+        w->ah2.ptr = q.A[mod3(w->step - 3)];
+    }
+}
+
+// Bind U[n % 2] and A[n % 3] to the waves' current buffers and load the step
+// counters (a wave may have been reset or stepped on its own since the last launch).
 static int batch_sync(iga_batch* b, cudaStream_t st) {
     bool dirty = false;
     for (int k = 0; k < b->nprob; ++k) {
         iga_wave* w = b->waves[k];
         BatchProb& q = b->hp[k];
+        float* A[3];
+        accel_buffers(w, A);
+        if (A[0] != q.A[0] || A[1] != q.A[1] || A[2] != q.A[2]) {
+            for (int j = 0; j < 3; ++j) q.A[j] = A[j];
+            dirty = true;
+        }
         if (q.U[w->step & 1] != w->u.ptr || q.U[(w->step + 1) & 1] != w->uprev.ptr ||
             q.L[w->step & 1] != w->ulo.ptr || q.L[(w->step + 1) & 1] != w->uprevlo.ptr) {
             q.U[w->step & 1] = w->u.as<float>();
@@ -480,7 +531,8 @@ extern "C" int iga_batch_create(int nprob, iga_wave* const* waves, iga_batch** o
         q.U[(w->step + 1) & 1] = w->uprev.as<float>();
         q.L[w->step & 1] = w->ulo.as<float>();
         q.L[(w->step + 1) & 1] = w->uprevlo.as<float>();
-        q.a = w->a.as<float>();
+        accel_buffers(w, q.A);
+        q.guess = w->desc.cg_guess;
         q.b = w->b.as<float>();
         q.r = (double*)take(8 * v);
         q.cu = (float*)take(4 * v);
@@ -578,12 +630,7 @@ extern "C" int iga_batch_step(iga_batch* b, int nsteps, int use_graph, void* str
     for (int k = 0; k < b->nprob; ++k) {
         iga_wave* w = b->waves[k];
         w->step += nsteps;
-        // keep the wave's view consistent: u = U[step % 2], uprev = the other
-        const BatchProb& q = b->hp[k];
-        w->u.ptr = q.U[w->step & 1];
-        w->uprev.ptr = q.U[(w->step + 1) & 1];
-        w->ulo.ptr = q.L[w->step & 1];
-        w->uprevlo.ptr = q.L[(w->step + 1) & 1];
+        wave_views(w, b->hp[k]);   // u = U[step % 2], a = A[(step - 1) % 3], ...
     }
     const int errw = (int)cnt[0];
     if (errw & 4) return fail(IGA_ERR_TIMEOUT, "partition barrier timed out in batch");
@@ -607,12 +654,7 @@ extern "C" int iga_batch_tune(iga_batch* b, int trial_steps, int rounds, void* s
         IGA_CUDA(cudaMemcpyAsync(clk.data(), b->hp[0].clk, sizeof(long long) * 2 * b->nprob, cudaMemcpyDeviceToHost, st));
         IGA_CUDA(cudaStreamSynchronize(st));
         for (auto* w : b->waves) w->step += trial_steps;
-        for (int k = 0; k < b->nprob; ++k) {
-            b->waves[k]->u.ptr = b->hp[k].U[b->waves[k]->step & 1];
-            b->waves[k]->uprev.ptr = b->hp[k].U[(b->waves[k]->step + 1) & 1];
-            b->waves[k]->ulo.ptr = b->hp[k].L[b->waves[k]->step & 1];
-            b->waves[k]->uprevlo.ptr = b->hp[k].L[(b->waves[k]->step + 1) & 1];
-        }
+        for (int k = 0; k < b->nprob; ++k) wave_views(b->waves[k], b->hp[k]);
         double mean = 0.0;
         std::vector<double> t(b->nprob);
         for (int k = 0; k < b->nprob; ++k) {

@@ -30,10 +30,10 @@ def _problems():
     return out
 
 
-def _wave(prob):
+def _wave(prob, guess=0):
     w, sp, ops, src, rec = prob
     return iga.iga_wave_create(ops, NSHOT, iga.IGA_F32, W.dt_of(w), src_pos=src, f0=10.0, t0=0.1, rec_pos=rec,
-                               nsteps_max=NSTEPS, cg_rtol=1e-6, cg_max_it=2000, cfl_check=0)
+                               nsteps_max=NSTEPS, cg_rtol=1e-6, cg_max_it=2000, cfl_check=0, cg_guess=guess)
 
 
 def _state(wave, ops):
@@ -44,16 +44,19 @@ def _state(wave, ops):
     return u.cpu().numpy().astype(np.float64)
 
 
-def test_batch_matches_individual_waves_and_graph_replay_is_exact():
+@pytest.mark.parametrize("guess", [0, 2])
+def test_batch_matches_individual_waves_and_graph_replay_is_exact(guess):
+    """guess: the waves' CG start order (2: quadratic extrapolation in time, whose three
+    acceleration buffers rotate inside the kernel and across graph replays)."""
     probs = _problems()
-    singles = [_wave(p) for p in probs]
+    singles = [_wave(p, guess) for p in probs]
     for wv in singles:
         iga.iga_wave_step(wv, NSTEPS)
-    batched = [_wave(p) for p in probs]
+    batched = [_wave(p, guess) for p in probs]
     b = iga.iga_batch_create(batched)
     for _ in range(3):                       # 10 + 10 + 10 steps through the captured graph
         iga.iga_batch_step(b, NSTEPS // 3, use_graph=True)
-    direct = [_wave(p) for p in probs]
+    direct = [_wave(p, guess) for p in probs]
     b2 = iga.iga_batch_create(direct)
     iga.iga_batch_step(b2, NSTEPS, use_graph=False)
     for k, p in enumerate(probs):
@@ -88,5 +91,28 @@ def test_batch_tuner_rebalances_and_keeps_results():
         iga.iga_wave_step(wv, NSTEPS)
     for k, p in enumerate(probs):
         err = np.linalg.norm(_state(waves[k], p[2]) - _state(singles[k], p[2])) / np.linalg.norm(_state(singles[k], p[2]))
+        assert err <= 1e-5
+    iga.iga_batch_destroy(b)
+
+
+def test_batch_continues_waves_stepped_on_their_own_with_extrapolated_start():
+    """A wave stepped alone for a few steps (its acceleration buffers rotated on the
+    host) and then batched continues the same scheme as a wave stepped alone throughout."""
+    probs = _problems()
+    singles = [_wave(p, 2) for p in probs]
+    for wv in singles:
+        iga.iga_wave_step(wv, NSTEPS)
+    mixed = [_wave(p, 2) for p in probs]
+    for wv in mixed:
+        iga.iga_wave_step(wv, 7)
+    b = iga.iga_batch_create(mixed)
+    iga.iga_batch_step(b, 11, use_graph=True)
+    for wv in mixed:                         # back to single stepping, then batched again
+        iga.iga_wave_step(wv, 4)
+    iga.iga_batch_step(b, NSTEPS - 22, use_graph=True)
+    for k, p in enumerate(probs):
+        us, um = _state(singles[k], p[2]), _state(mixed[k], p[2])
+        err = np.linalg.norm(um - us) / np.linalg.norm(us)
+        print("mesh", SIZES[k], "mixed vs single relative L2", err)
         assert err <= 1e-5
     iga.iga_batch_destroy(b)
