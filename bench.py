@@ -290,6 +290,41 @@ def run_ours(args, rank, world, device):
     return out, (space, ops, wave, w, nsteps, dt, src, rec)
 
 
+def stencil_apply_leg(ctx, args):
+    """Stand-alone FP32 K~ and M~ applies (one right-hand side) on the bench operator:
+    CUDA events on the launching stream around 20 back-to-back launches (the fields are
+    larger than L2, so every launch streams them from HBM), algorithmic bytes = every
+    stored field element once + x read + y written."""
+    import torch
+
+    from paper_2004_05197_gb300 import iga
+    space, ops, wave, w, nsteps, dt, src, rec = ctx
+    info = iga.iga_ops_info_get(ops)
+    N = info.N
+    peaks = load_peaks()
+    peak = (peaks or {}).get("hbm_gbs") or HBM_FALLBACK_GBS
+    stream = torch.cuda.current_stream()
+    x = torch.rand((1, N), device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    res = {}
+    for name, which, nf in (("K", iga.IGA_OP_K, info.nK), ("M", iga.IGA_OP_M, info.nM)):
+        for _ in range(3):
+            iga.iga_stencil_apply(ops, which, iga.IGA_F32, x, y, 1, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            iga.iga_stencil_apply(ops, which, iga.IGA_F32, x, y, 1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        gbs = (nf * 4 + 8) * N / (us * 1e-6) / 1e9
+        res["stencil_apply_fp32_" + name] = {"us": us, "fields": nf, "bytes_per_row": nf * 4 + 8,
+                                            "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+    return res
+
+
 def fp64_plain_and_error(ctx, args):
     """FP64 plain single-shot schedule on the same workload (bounded steps) and the FP32 error."""
     import numpy as np
@@ -684,6 +719,7 @@ def main():
     __graft_entry__.build()
     out, ctx = run_ours(args, rank, world, device)
     if rank == 0:
+        out["components"].update(stencil_apply_leg(ctx, args))
         if not args.no_compare:
             out["components"].update(fp64_plain_and_error(ctx, args))
         if args.e2e_steps > 0:

@@ -21,9 +21,10 @@ __global__ void __launch_bounds__(256) apply_kernel(const T* __restrict__ F, lon
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         T acc[R], own[R];
         if (i >= dmax && i < N - dmax)
-            stencil_row_interior<DIM, P, T, MASS, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, sdl, acc, own);
+            stencil_row_interior<DIM, P, T, MASS, R, (R >= 4 ? 2 : 16), LdgLoad<T>, true>(F, pitch, ld, i, sdl, acc,
+                                                                                     own);
         else
-            stencil_row<DIM, P, T, MASS, R, (R >= 4 ? 2 : 4)>(F, pitch, ld, i, N, m, acc, own);
+            stencil_row<DIM, P, T, MASS, R, (R >= 4 ? 2 : 4), LdgLoad<T>, true>(F, pitch, ld, i, N, m, acc, own);
 #pragma unroll
         for (int r = 0; r < R; ++r) y[(size_t)r * N + i] = acc[r];
     }
