@@ -268,8 +268,8 @@ def run_ours(args, rank, world, device):
         "config": {"workload": args.workload, "dim": w["dim"], "p": w["p"], "n_el": w["n_el"], "N": N,
                    "q": w["q"], "M": w["M"], "nsteps": nsteps, "nshot": args.nshot, "cg_rtol": args.cg_rtol,
                    "cg_schedule": args.solve,
-                   "cg_start": ["previous acceleration", "linear extrapolation in time",
-                                "quadratic extrapolation in time"][args.cg_guess],
+                   "cg_start": ("previous acceleration" if args.cg_guess == 0 else
+                                "polynomial extrapolation in time, order %d" % args.cg_guess),
                    "precision": "FP32 fields/vectors/apply, FP64 quadrature, residual and dot products",
                    "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (
                        (oinfo.nK + oinfo.nM) * oinfo.pitch * 12 / 1e9),
@@ -438,7 +438,7 @@ def run_batched(args):
             waves.append(iga.iga_wave_create(ops, 8, iga.IGA_F32, W.dt_of(w), src_pos=src[8 * g:8 * g + 8],
                                              f0=10.0, t0=0.1, rec_pos=np.array([[0.5, 0.5]]), nsteps_max=nsteps + 64,
                                              cg_rtol=args.batched_rtol, cg_max_it=args.cg_max_it, cfl_check=2,
-                                             cg_guess=args.cg_guess))
+                                             cg_guess=args.batched_cg_guess))
     b = iga.iga_batch_create(waves)
     iga.iga_batch_tune(b, trial_steps=5, rounds=3)
     part = iga.iga_batch_partition(b, len(waves))
@@ -472,7 +472,7 @@ def run_batched(args):
     for k, (w, sp, ops, src) in enumerate(meshes):
         wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
                                  cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN,
-                                 cfl_check=0, cg_guess=args.cg_guess)
+                                 cfl_check=0, cg_guess=args.batched_cg_guess)
         torch.cuda.synchronize()
         t = time.perf_counter()
         iga.iga_wave_step(wv, args.plain_steps)
@@ -481,7 +481,7 @@ def run_batched(args):
         plain_ss += args.plain_steps
         iga.iga_wave_destroy(wv)
         wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
-                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, cfl_check=0, cg_guess=args.cg_guess)
+                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, cfl_check=0, cg_guess=args.batched_cg_guess)
         iga.iga_wave_step(wv, nsteps)
         N = iga.iga_ops_info_get(ops).N
         u = torch.empty((1, N), dtype=torch.float64, device="cuda")
@@ -500,7 +500,9 @@ def run_batched(args):
             "plain_fp64_single_shot_shot_steps_per_s": plain,
             "batched_over_plain": batched / plain,
             "batched_fp32_vs_fp64_rel_l2_error_max": max(errs),
-            "batched_partition_blocks": part}
+            "batched_partition_blocks": part,
+            "batched_cg_start": ("previous acceleration" if args.batched_cg_guess == 0 else
+                                 "polynomial extrapolation in time, order %d" % args.batched_cg_guess)}
 
 
 def run_adjoint(args):
@@ -682,8 +684,8 @@ def main():
     ap.add_argument("--nshot", type=int, default=1)
     ap.add_argument("--cg-rtol", type=float, default=1e-6)
     ap.add_argument("--cg-max-it", type=int, default=2000)
-    ap.add_argument("--cg-guess", type=int, default=2, choices=[0, 1, 2],
-                    help="CG start of each step: a^{n-1} (0), linear (1) or quadratic (2) extrapolation")
+    ap.add_argument("--cg-guess", type=int, default=3, choices=range(7),
+                    help="CG start of each step: polynomial extrapolation in time of this order (0: a^{n-1})")
     ap.add_argument("--solve", default="persistent", choices=["persistent", "graph"],
                     help="CG schedule of the FP32 waves")
     ap.add_argument("--compare-steps", type=int, default=50)
@@ -696,6 +698,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--batched-rtol", type=float, default=3e-7,
                     help="CG tolerance of the batched FP32 shots (the CG term of the FP32 error is about 15 rtol after 1000 steps)")
+    ap.add_argument("--batched-cg-guess", type=int, default=3, choices=range(7),
+                    help="CG start order of the batched leg and of its plain FP64 comparison")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--adjoint", action="store_true",
                     help="also run the adjoint-gradient leg (several minutes: FP64 forward / reverse sweeps)")

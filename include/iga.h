@@ -252,6 +252,8 @@ int iga_ops_spectrum(const iga_ops* ops, int dtype, int k, double* lambda_min, d
  * r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), t_n = n dt.
  * Receivers record d^n = sum_i u_i^n B_i(s_rec) after every step.
  */
+#define IGA_CG_GUESS_MAX 6   /* highest extrapolation order of the CG start (cg_guess) */
+
 typedef struct iga_wave_desc {
     int nshot;                  /* independent shots advanced together (multi-RHS) */
     int dtype;                  /* IGA_F32 or IGA_F64 */
@@ -271,13 +273,15 @@ typedef struct iga_wave_desc {
     int cfl_check;              /* 1: estimate lambda_max(M~^-1 K~) by Lanczos at create and at every
                                    reset; 2: at create only; 0: off.  With an estimate, steps
                                    with dt sqrt(lambda_max) >= 2 are refused (IGA_ERR_ARG) */
-    int cg_guess;               /* initial guess of step n's mass solve: 0 = a^{n-1};
-                                   1 = 2 a^{n-1} - a^{n-2} (linear extrapolation in time);
-                                   2 = 3 a^{n-1} - 3 a^{n-2} + a^{n-3} (quadratic).  The order
-                                   drops to what the steps done so far allow (a^{-1} = 0 at n = 0,
-                                   order 0 at n = 1, at most order 1 at n = 2).  Only the
-                                   starting point of the CG changes; every solve still runs to
-                                   cg_rtol.  wave_adjoint runs its forward sweeps with order 0 */
+    int cg_guess;               /* start of step n's mass solve: the polynomial extrapolation in
+                                   time of order K = cg_guess (0..IGA_CG_GUESS_MAX) through the last
+                                   K + 1 accelerations, sum_{j=0..K} (-1)^j C(K+1, j+1) a^{n-1-j}:
+                                   0 = a^{n-1}; 1 = 2a^{n-1} - a^{n-2}; 2 = 3a^{n-1} - 3a^{n-2} +
+                                   a^{n-3}; ...  The order drops to what the steps done so far
+                                   allow (a^{-1} = 0 at n = 0, order min(K, n - 1) after).  Only
+                                   the starting point of the CG changes; every solve still runs
+                                   to cg_rtol.  K extra acceleration vectors per shot are kept.
+                                   wave_adjoint runs its forward sweeps with order 0 */
 } iga_wave_desc;
 
 int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);

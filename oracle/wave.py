@@ -18,6 +18,8 @@ receiver model are the workload's:
   Greville points gamma_i, v^0 = 0;
 * receiver traces d_r^n = sum_i u_i^n B_i(s_r), recorded for n = 1..nsteps.
 """
+from math import comb
+
 import numpy as np
 import scipy.sparse as sps
 
@@ -77,19 +79,20 @@ def gaussian_pulse(space, xc, width):
 
 def cg_start(hist, order, n):
     """Start of step n's mass solve from the accelerations of the earlier steps,
-    hist = [a^{n-1}, a^{n-2}, a^{n-3}] (as many as exist): zero before the first
-    step, else the polynomial extrapolation in time of degree min(order, len - 1)
-    through the last points (degree 0: a^{n-1}; 1: 2a^{n-1} - a^{n-2};
-    2: 3a^{n-1} - 3a^{n-2} + a^{n-3}).  The starting point is not part of the
-    time-stepping scheme: every solve still runs to its tolerance."""
+    hist = [a^{n-1}, a^{n-2}, ...] (most recent first, as many as exist): zero
+    before the first step, else the value one step ahead of the polynomial of
+    degree k = min(order, len(hist) - 1) through the last k + 1 accelerations,
+    sum_{j=0..k} (-1)^j C(k+1, j+1) a^{n-1-j} (Newton's backward differences:
+    degree 0: a^{n-1}; 1: 2a^{n-1} - a^{n-2}; 2: 3a^{n-1} - 3a^{n-2} + a^{n-3}).
+    The starting point is not part of the time-stepping scheme: every solve
+    still runs to its tolerance."""
     if not hist:
         return np.zeros(n)
     k = min(order, len(hist) - 1)
-    if k == 0:
-        return hist[0].copy()
-    if k == 1:
-        return 2.0 * hist[0] - hist[1]
-    return 3.0 * (hist[0] - hist[1]) + hist[2]
+    out = np.zeros(n)
+    for j in range(k + 1):
+        out += (-1) ** j * comb(k + 1, j + 1) * hist[j]
+    return out
 
 
 class Leapfrog:
@@ -131,7 +134,7 @@ class Leapfrog:
             else:
                 u_new = 2.0 * u - u_prev + dt * dt * a
             u_prev, u = u, u_new
-            hist = [a] + hist[:2]
+            hist = [a] + hist[:self.guess_order]
             if len(receivers):
                 traces[:, n] = rvec @ u
         return u, u_prev, traces

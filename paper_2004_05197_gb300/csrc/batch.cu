@@ -12,8 +12,8 @@
 //   update          u^{n+1} = 2u^n - u^{n-1} + dt^2 a^n  (n = 0: u^0 + dt^2/2 a^0) into U[(n+1) mod 2]
 //   barrier, receivers of u^{n+1}
 // FP32 fields and state, FP64 residual and reductions (as mass_solve).  The CG
-// start of step n follows the wave's cg_guess (a^{n-1}, or its linear / quadratic
-// extrapolation in time from the accelerations in A[(n-1..n-3) % 3]).
+// start of step n follows the wave's cg_guess K (a^{n-1}, or the polynomial
+// extrapolation in time through the accelerations in A[(n-1..n-1-K) % (K+1)]).
 // The step counter lives in device memory, so one captured graph of the launch
 // can be replayed for consecutive step ranges.
 #include <algorithm>
@@ -42,8 +42,9 @@ struct BatchProb {
     int N, m;
     float* U[2];        // u^n in U[n % 2]
     float* L[2];        // low parts of the compensated state, alongside U
-    float* A[3];        // CG solutions: a^n in A[n % 3] (one buffer three times when guess = 0)
-    int guess;          // CG start order (the wave's cg_guess): 0 = a^{n-1} in place
+    float* A[IGA_CG_GUESS_MAX + 1];   // CG solutions: a^n in A[n % ring]
+    int guess;          // CG start order K (the wave's cg_guess): 0 = a^{n-1} in place
+    int ring;           // K + 1 acceleration buffers (1 when K = 0)
     float* b;           // right-hand side
     double* r;          // CG residual (FP64)
     float* cu;          // D^-1 r
@@ -103,19 +104,27 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchProb* __
         float* nxt = q.U[(n + 1) & 1];   // holds u^{n-1}; receives u^{n+1}
         const float* curlo = q.L[n & 1];
         float* nxtlo = q.L[(n + 1) & 1];
-        float* const qa = q.A[n % 3];   // receives a^n; holds the CG start
-        // ---- CG start extrapolated in time into A[n % 3] (which held a^{n-3}); the
-        // force phase's barrier orders it before the mass apply of CG init 1
+        float* const qa = q.A[n % q.ring];   // receives a^n; holds the CG start
+        // ---- CG start extrapolated in time, sum_j (-1)^j C(k+1, j+1) a^{n-1-j}, into
+        // A[n % ring] (which held a^{n-1-K}, the oldest term); the force phase's
+        // barrier orders it before the mass apply of CG init 1
         if (q.guess > 0 && n >= 1) {
-            const int order = min(q.guess, n - 1);
-            const float* h0 = q.A[(n + 2) % 3];   // a^{n-1}
-            const float* h1 = q.A[(n + 1) % 3];   // a^{n-2}
+            const int k = min(q.guess, n - 1);
+            float c[IGA_CG_GUESS_MAX + 1];
+            const float* h[IGA_CG_GUESS_MAX + 1];
+            for (int j = 0; j <= k; ++j) {
+                double bc = 1.0;
+                for (int t = 1; t <= j + 1; ++t) bc = bc * (k + 2 - t) / t;
+                c[j] = (float)((j & 1) ? -bc : bc);
+                h[j] = q.A[(n - 1 - j + q.ring) % q.ring];
+            }
             for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const long long o = (long long)r * q.ld + i;
-                    const float a0 = h0[o];
-                    qa[o] = order == 0 ? a0 : order == 1 ? 2.f * a0 - h1[o] : 3.f * (a0 - h1[o]) + qa[o];
+                    float v = 0.f;
+                    for (int j = 0; j <= k; ++j) v += c[j] * h[j][o];
+                    qa[o] = v;
                 }
         }
         // ---- force + source
@@ -393,18 +402,16 @@ static int upload_probs(iga_batch* b, cudaStream_t st) {
 // then 2 clocks per problem
 static int* batch_err(iga_batch* b) { return (int*)b->counters.as<long long>(); }
 
-static int mod3(int n) { return ((n % 3) + 3) % 3; }
+static int ring_of(const iga_wave* w) { return w->desc.cg_guess + 1; }
+static int modr(int n, int r) { return ((n % r) + r) % r; }
 
-// The wave keeps a^{step-1}, a^{step-2}, a^{step-3} in a, ah1, ah2 (cg_guess > 0);
-// the kernel finds a^n in A[n % 3].
-static void accel_buffers(const iga_wave* w, float* A[3]) {
-    if (w->desc.cg_guess > 0) {
-        A[mod3(w->step - 1)] = w->a.as<float>();
-        A[mod3(w->step - 2)] = w->ah1.as<float>();
-        A[mod3(w->step - 3)] = w->ah2.as<float>();
-    } else {
-        A[0] = A[1] = A[2] = w->a.as<float>();
-    }
+// The wave keeps a^{step-1} in a and a^{step-2-j} in ah[j] (j < cg_guess); the
+// kernel finds a^n in A[n % ring].
+static void accel_buffers(const iga_wave* w, float* A[IGA_CG_GUESS_MAX + 1]) {
+    const int R = ring_of(w);
+    for (int j = 0; j <= IGA_CG_GUESS_MAX; ++j) A[j] = nullptr;
+    A[modr(w->step - 1, R)] = w->a.as<float>();
+    for (int j = 0; j + 1 < R; ++j) A[modr(w->step - 2 - j, R)] = w->ah[j].as<float>();
 }
 
 // After steps ran in the kernel: the wave's u / uprev / a views for its new step.
@@ -413,11 +420,9 @@ static void wave_views(iga_wave* w, const BatchProb& q) {
     w->uprev.ptr = q.U[(w->step + 1) & 1];
     w->ulo.ptr = q.L[w->step & 1];
     w->uprevlo.ptr = q.L[(w->step + 1) & 1];
-    if (w->desc.cg_guess > 0) {
-        w->a.ptr = q.A[mod3(w->step - 1)];
-        w->ah1.ptr = q.A[mod3(w->step - 2)];
-        w->ah2.ptr = q.A[mod3(w->step - 3)];
-    }
+    const int R = ring_of(w);
+    w->a.ptr = q.A[modr(w->step - 1, R)];
+    for (int j = 0; j + 1 < R; ++j) w->ah[j].ptr = q.A[modr(w->step - 2 - j, R)];
 }
 
 // Bind U[n % 2] and A[n % 3] to the waves' current buffers and load the step
@@ -427,12 +432,13 @@ static int batch_sync(iga_batch* b, cudaStream_t st) {
     for (int k = 0; k < b->nprob; ++k) {
         iga_wave* w = b->waves[k];
         BatchProb& q = b->hp[k];
-        float* A[3];
+        float* A[IGA_CG_GUESS_MAX + 1];
         accel_buffers(w, A);
-        if (A[0] != q.A[0] || A[1] != q.A[1] || A[2] != q.A[2]) {
-            for (int j = 0; j < 3; ++j) q.A[j] = A[j];
-            dirty = true;
-        }
+        for (int j = 0; j <= IGA_CG_GUESS_MAX; ++j)
+            if (A[j] != q.A[j]) {
+                q.A[j] = A[j];
+                dirty = true;
+            }
         if (q.U[w->step & 1] != w->u.ptr || q.U[(w->step + 1) & 1] != w->uprev.ptr ||
             q.L[w->step & 1] != w->ulo.ptr || q.L[(w->step + 1) & 1] != w->uprevlo.ptr) {
             q.U[w->step & 1] = w->u.as<float>();
@@ -533,6 +539,7 @@ extern "C" int iga_batch_create(int nprob, iga_wave* const* waves, iga_batch** o
         q.L[(w->step + 1) & 1] = w->uprevlo.as<float>();
         accel_buffers(w, q.A);
         q.guess = w->desc.cg_guess;
+        q.ring = ring_of(w);
         q.b = w->b.as<float>();
         q.r = (double*)take(8 * v);
         q.cu = (float*)take(4 * v);

@@ -101,7 +101,7 @@ struct iga_wave {
     long long N;
     iga::DevBuf u, uprev, a, b, traces, src_idx, src_w, rec_idx, rec_w, work, counters;
     iga::DevBuf ulo, uprevlo;        // FP32 waves: low parts of the compensated state (hi + lo)
-    iga::DevBuf ah1, ah2;            // cg_guess > 0: a^{n-2}, a^{n-3} (a holds a^{n-1} between steps)
+    iga::DevBuf ah[IGA_CG_GUESS_MAX];   // cg_guess = K > 0: ah[j] = a^{n-2-j}, j < K (a holds a^{n-1})
     iga::DevBuf greville, centres;   // pulse initial condition inputs (GAUSS_PULSE)
     int timing = 0;
     long long cg_solves = 0;

@@ -179,19 +179,33 @@ static double ricker(double t, double f0, double t0) {
     return (1.0 - 2.0 * a) * std::exp(-a);
 }
 
-// Extrapolated start of step n's mass solve, written over the oldest history
-// buffer x = a^{n-3}: order 0: x = a^{n-1}; 1: x = 2 a^{n-1} - a^{n-2};
-// 2: x = 3 a^{n-1} - 3 a^{n-2} + a^{n-3}.  Exact for accelerations that are
-// polynomials of that order in time; any rounding only moves the CG start.
+// Extrapolated start of step n's mass solve, x = sum_{j<=k} c_j h_j with
+// h_j = a^{n-1-j} and c_j = (-1)^j C(k+1, j+1) (the polynomial of degree k through
+// the last k + 1 accelerations, evaluated one step ahead; exact for accelerations
+// that are polynomials of that degree in time).  x may be the buffer of h_k (the
+// oldest term), which every element reads before it is written; any rounding only
+// moves the CG start.
 template <typename T>
-__global__ void guess_kernel(T* __restrict__ x, const T* __restrict__ h0, const T* __restrict__ h1, long long tot,
-                             int order) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot;
-         k += (long long)gridDim.x * blockDim.x) {
-        const T a0 = h0[k];
-        if (order == 0) x[k] = a0;
-        else if (order == 1) x[k] = T(2) * a0 - h1[k];
-        else x[k] = T(3) * (a0 - h1[k]) + x[k];
+struct GuessTerms {
+    const T* h[IGA_CG_GUESS_MAX + 1];
+    float c[IGA_CG_GUESS_MAX + 1];
+    int k;
+};
+
+__host__ __device__ inline float guess_coeff(int k, int j) {
+    // (-1)^j C(k+1, j+1)
+    double b = 1.0;
+    for (int t = 1; t <= j + 1; ++t) b = b * (k + 2 - t) / t;
+    return (float)((j & 1) ? -b : b);
+}
+
+template <typename T>
+__global__ void guess_kernel(T* x, GuessTerms<T> g, long long tot) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        T v = T(0);
+        for (int j = 0; j <= g.k; ++j) v += (T)g.c[j] * g.h[j][i];
+        x[i] = v;
     }
 }
 
@@ -229,23 +243,29 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
             IGA_LAUNCH_CHECK("source_kernel");
         }
         // start of the solve: a^{n-1} in place (cg_guess 0, or n = 0 with a^{-1} = 0), else
-        // the extrapolation from the last three accelerations written into the oldest buffer
-        const bool extrap = w->desc.cg_guess > 0 && n >= 1;
+        // the extrapolation from the last accelerations written into the oldest buffer
+        const int K = w->desc.cg_guess;
+        const bool extrap = K > 0 && n >= 1;
         if (extrap) {
-            guess_kernel<T><<<ugrid, 256, 0, st>>>(w->ah2.as<T>(), w->a.as<T>(), w->ah1.as<T>(), tot,
-                                                   std::min(w->desc.cg_guess, n - 1));
+            GuessTerms<T> g;
+            g.k = std::min(K, n - 1);
+            for (int j = 0; j <= g.k; ++j) {
+                g.h[j] = j == 0 ? w->a.as<T>() : w->ah[j - 1].as<T>();
+                g.c[j] = guess_coeff(g.k, j);
+            }
+            guess_kernel<T><<<ugrid, 256, 0, st>>>(w->ah[K - 1].as<T>(), g, tot);
             IGA_LAUNCH_CHECK("guess_kernel");
         }
         if (w->timing) cudaEventRecord(ev[4 * s + 2], st);
-        void* xsol = extrap ? w->ah2.ptr : w->a.ptr;
+        void* xsol = extrap ? w->ah[K - 1].ptr : w->a.ptr;
         rc = mass_solve_impl(ops, w->dtype, w->b.ptr, xsol, w->N, w->nshot, w->desc.cg_rtol, w->desc.cg_max_it,
                              w->desc.solve_flags, nullptr, nullptr, st, w->work.ptr, w->work.bytes, iter_acc, status);
         if (extrap) {
-            // a <- a^n, ah1 <- a^{n-1}, ah2 <- a^{n-2}
+            // a <- a^n, ah[j] <- a^{n-1-j}
             void* old_a = w->a.ptr;
-            w->a.ptr = w->ah2.ptr;
-            w->ah2.ptr = w->ah1.ptr;
-            w->ah1.ptr = old_a;
+            w->a.ptr = w->ah[K - 1].ptr;
+            for (int j = K - 1; j > 0; --j) w->ah[j].ptr = w->ah[j - 1].ptr;
+            w->ah[0].ptr = old_a;
         }
         if (w->timing) cudaEventRecord(ev[4 * s + 3], st);
         w->cg_solves += (w->nshot + 3) / 4;
@@ -298,8 +318,8 @@ int wave_initial_state(iga_wave* w, cudaStream_t st) {
     const iga_space* s = w->ops->space;
     const size_t vb = (w->dtype == IGA_F64 ? 8 : 4) * (size_t)w->nshot * w->N;
     IGA_CUDA(cudaMemsetAsync(w->a.ptr, 0, vb, st));
-    if (w->ah1.ptr) IGA_CUDA(cudaMemsetAsync(w->ah1.ptr, 0, vb, st));
-    if (w->ah2.ptr) IGA_CUDA(cudaMemsetAsync(w->ah2.ptr, 0, vb, st));
+    for (auto& h : w->ah)
+        if (h.ptr) IGA_CUDA(cudaMemsetAsync(h.ptr, 0, vb, st));
     IGA_CUDA(cudaMemsetAsync(w->uprev.ptr, 0, vb, st));
     if (w->dtype == IGA_F32) {
         IGA_CUDA(cudaMemsetAsync(w->ulo.ptr, 0, vb, st));
@@ -383,7 +403,7 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
     if (d.init_kind == IGA_INIT_GAUSS_PULSE && (!d.pulse_centre || !(d.pulse_width > 0)))
         return fail(IGA_ERR_ARG, "GAUSS_PULSE needs centres and a positive width");
     if (d.with_source && !d.src_pos) return fail(IGA_ERR_ARG, "source positions missing");
-    if (d.cg_guess < 0 || d.cg_guess > 2) return fail(IGA_ERR_ARG, "cg_guess must be 0, 1 or 2");
+    if (d.cg_guess < 0 || d.cg_guess > IGA_CG_GUESS_MAX) return fail(IGA_ERR_ARG, "cg_guess must be in 0..6");
     if (d.nrec > 0 && !d.rec_pos) return fail(IGA_ERR_ARG, "receiver positions missing");
     const iga_space* s = ops->space;
     iga_wave* w = new (std::nothrow) iga_wave();
@@ -413,8 +433,7 @@ extern "C" int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, ig
     if (!rc) rc = w->work.alloc(mass_solve_work_bytes(ops, d.dtype, d.nshot));
     if (!rc && d.dtype == IGA_F32) rc = w->ulo.alloc(vb);
     if (!rc && d.dtype == IGA_F32) rc = w->uprevlo.alloc(vb);
-    if (!rc && d.cg_guess > 0) rc = w->ah1.alloc(vb);
-    if (!rc && d.cg_guess > 0) rc = w->ah2.alloc(vb);
+    for (int j = 0; j < d.cg_guess && !rc; ++j) rc = w->ah[j].alloc(vb);
     if (rc) return bail(rc);
     // source / receiver tables
     std::vector<int> idx;

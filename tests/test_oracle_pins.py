@@ -383,21 +383,25 @@ def test_leapfrog_eigenmode_closed_form():
 
 def test_cg_start_reproduces_polynomials_in_time():
     """The extrapolated CG start is exact on accelerations a^n that are polynomials in
-    n of the extrapolation degree, and the degree drops to what the history allows."""
+    n of the extrapolation degree (and not on one degree higher), and the degree drops
+    to what the history allows."""
     from oracle.wave import cg_start
     rng = np.random.default_rng(7)
-    c0, c1, c2 = rng.standard_normal((3, 11))
-    a = lambda n: c0 + c1 * n + c2 * n * n
-    n = 9
-    hist = [a(n - 1), a(n - 2), a(n - 3)]
-    np.testing.assert_allclose(cg_start(hist, 2, 11), a(n), rtol=0, atol=1e-12 * np.abs(a(n)).max())
-    lin = lambda n: c0 + c1 * n
-    np.testing.assert_allclose(cg_start([lin(n - 1), lin(n - 2), lin(n - 3)], 1, 11), lin(n), atol=1e-13)
-    # a quadratic is not reproduced by the linear rule (the c2 term is missed by 2 c2)
-    assert np.abs(cg_start(hist, 1, 11) - a(n)).max() > 0.1 * np.abs(c2).max()
+    n = 12
+    for deg in (0, 1, 2, 3, 6):
+        c = rng.standard_normal((deg + 2, 11))
+        poly = lambda t, d: sum(c[i] * float(t) ** i for i in range(d + 1))
+        hist = [poly(n - 1 - j, deg) for j in range(deg + 1)]
+        want = poly(n, deg)
+        np.testing.assert_allclose(cg_start(hist, deg, 11), want, rtol=0, atol=1e-9 * np.abs(want).max())
+        # one degree more is not reproduced by this order
+        hist1 = [poly(n - 1 - j, deg + 1) for j in range(deg + 1)]
+        assert np.abs(cg_start(hist1, deg, 11) - poly(n, deg + 1)).max() > 1e-3 * np.abs(c[deg + 1]).max()
+    h = [rng.standard_normal(11) for _ in range(3)]
     assert np.array_equal(cg_start([], 2, 11), np.zeros(11))
-    assert np.array_equal(cg_start(hist[:1], 2, 11), hist[0])
-    np.testing.assert_allclose(cg_start(hist[:2], 2, 11), 2 * hist[0] - hist[1])
+    assert np.array_equal(cg_start(h[:1], 2, 11), h[0])
+    np.testing.assert_allclose(cg_start(h[:2], 2, 11), 2 * h[0] - h[1])
+    np.testing.assert_allclose(cg_start(h, 2, 11), 3 * h[0] - 3 * h[1] + h[2])
 
 
 def test_leapfrog_extrapolated_start_same_solution_fewer_iterations():
