@@ -521,45 +521,53 @@ extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigne
         cudaMemsetAsync(ops->status.ptr, 0, ops->status.bytes, st) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "cudaMemsetAsync"));
 
-    EventTimer tm;
-    cudaEventRecord(tm.ev[0], st);
-    // ---- a3: band (or all) elements, grouped by colour
+    // ---- a0: band (or all) elements grouped by colour for a3 (an index set of the mesh,
+    // built once per space and kept on the device)
     const int ne = s->n_el, P1 = p + 1;
-    std::vector<std::vector<int>> colour(1 << 0);
     int ncol = 1;
     for (int k = 0; k < dim; ++k) ncol *= P1;
-    colour.assign(ncol, std::vector<int>());
-    long long nel_total = 1;
-    for (int k = 0; k < dim; ++k) nel_total *= ne;
-    for (long long el = 0; el < nel_total; ++el) {
-        int e[3] = {0, 0, 0};
-        long long r = el;
-        bool band = false;
-        int c = 0, cw = 1;
-        for (int k = 0; k < dim; ++k) {
-            e[k] = (int)(r % ne);
-            r /= ne;
-            band = band || e[k] <= 2 * p - 1 || e[k] >= ne - 2 * p;
-            c += (e[k] % P1) * cw;
-            cw *= P1;
+    const int lk = true_only ? 1 : 0;
+    if (s->band_offs[lk].empty()) {
+        std::vector<std::vector<int>> colour(ncol);
+        long long nel_total = 1;
+        for (int k = 0; k < dim; ++k) nel_total *= ne;
+        for (long long el = 0; el < nel_total; ++el) {
+            long long r = el;
+            bool band = false;
+            int c = 0, cw = 1;
+            for (int k = 0; k < dim; ++k) {
+                const int ek = (int)(r % ne);
+                r /= ne;
+                band = band || ek <= 2 * p - 1 || ek >= ne - 2 * p;
+                c += (ek % P1) * cw;
+                cw *= P1;
+            }
+            if (true_only || band) colour[c].push_back((int)el);
         }
-        if (true_only || band) colour[c].push_back((int)el);
+        std::vector<int> flat;
+        std::vector<int> offs(ncol + 1, 0);
+        for (int c = 0; c < ncol; ++c) {
+            offs[c] = (int)flat.size();
+            flat.insert(flat.end(), colour[c].begin(), colour[c].end());
+        }
+        offs[ncol] = (int)flat.size();
+        if ((rc = s->band_elems[lk].alloc(sizeof(int) * std::max<size_t>(1, flat.size())))) return bail(rc);
+        if (!flat.empty()) {
+            cudaError_t e = cudaMemcpy(s->band_elems[lk].ptr, flat.data(), sizeof(int) * flat.size(),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                s->band_elems[lk].release();
+                return bail(cuda_fail(e, "cudaMemcpy(elements)"));
+            }
+        }
+        s->band_offs[lk] = offs;
     }
-    std::vector<int> flat;
-    std::vector<int> offs(ncol + 1, 0);
-    for (int c = 0; c < ncol; ++c) {
-        offs[c] = (int)flat.size();
-        flat.insert(flat.end(), colour[c].begin(), colour[c].end());
-    }
-    offs[ncol] = (int)flat.size();
-    ops->n_band = (int)flat.size();
-    DevBuf d_elems;
-    if ((rc = d_elems.alloc(sizeof(int) * std::max<size_t>(1, flat.size())))) return bail(rc);
-    if (!flat.empty()) {
-        cudaError_t e = cudaMemcpyAsync(d_elems.ptr, flat.data(), sizeof(int) * flat.size(),
-                                        cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpyAsync(elements)"));
-    }
+    const std::vector<int>& offs = s->band_offs[lk];
+    ops->n_band = offs[ncol];
+    const DevBuf& d_elems = s->band_elems[lk];
+    EventTimer tm;
+    cudaEventRecord(tm.ev[0], st);
+    // ---- a3: band quadrature, one launch per colour
     band_fn bf = pick_band(dim, p);
     for (int c = 0; c < ncol; ++c) {
         const int cnt = offs[c + 1] - offs[c];

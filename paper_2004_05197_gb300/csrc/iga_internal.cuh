@@ -77,6 +77,10 @@ struct iga_space {
     std::vector<double> tval_h;             // [n_el][nq][theta_deg+1] theta basis values (host copy)
     iga::DevBuf theta, qs, qw, bval, bder, tspan, tval;
     iga::GeomParams gp;
+    // element lists of the band quadrature, grouped by colour, built on the first
+    // assembly that needs them ([0]: boundary band, [1]: every element)
+    iga::DevBuf band_elems[2];
+    std::vector<int> band_offs[2];
 };
 
 struct iga_ops {

@@ -141,6 +141,28 @@ def test_assembly_is_deterministic():
     iga.iga_ops_destroy(b)
 
 
+def test_assembly_reuses_the_space_band_lists():
+    """The band element lists are built once per space (one for the surrogate band, one
+    for TRUE_ONLY): alternating assemblies on one space give the fields of fresh spaces."""
+    name = "annulus40_p3_sincos"
+    w = CASES[name]()
+    space = W.make_space(w)
+    a = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"])
+    t = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"], iga.IGA_TRUE_ONLY)
+    b = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"])
+    _, fresh = gpu_ops(name)
+    _, fresh_t = gpu_ops(name, flags=iga.IGA_TRUE_ONLY)
+    for which in (iga.IGA_OP_K, iga.IGA_OP_M):
+        ref = fields(fresh, which, iga.IGA_F64)
+        assert np.array_equal(fields(a, which, iga.IGA_F64), ref)
+        assert np.array_equal(fields(b, which, iga.IGA_F64), ref)
+        assert np.array_equal(fields(t, which, iga.IGA_F64), fields(fresh_t, which, iga.IGA_F64))
+    assert iga.iga_ops_info_get(a).n_band_elements == iga.iga_ops_info_get(fresh).n_band_elements
+    for o in (a, t, b):
+        iga.iga_ops_destroy(o)
+    iga.iga_space_destroy(space)
+
+
 def _apply_case(name, which, dtype, nrhs):
     sp, S, SK, SM, _, _ = oracle_full(name)
     _, ops = gpu_ops(name)
