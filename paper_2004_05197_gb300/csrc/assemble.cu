@@ -13,9 +13,11 @@
 //  a4  interp_dir_kernel   : B-spline interpolation coefficients of every stencil
 //                            function (Sec. 3.3), one direction at a time with the
 //                            precomputed inverse of the 1-D collocation matrix.
-//  a5  eval_kernel         : surrogate values K~_delta(x~_i), M~_delta(x~_i) at every
-//                            interior row whose neighbour i+delta is interior
-//                            (Eq. DefinitionOfSurrogateMatrixSymmetric / ..Kernel).
+//  a5  eval_dir_kernel,    : surrogate values K~_delta(x~_i), M~_delta(x~_i) at every
+//      eval_last_kernel      interior row whose neighbour i+delta is interior
+//                            (Eq. DefinitionOfSurrogateMatrixSymmetric / ..Kernel),
+//                            the tensor-product interpolant contracted one direction
+//                            at a time over the grid of interior rows.
 //      finalize_kernel     : FP32 copies of the fields, inverse Jacobi diagonal of
 //                            M~, non-finite check.
 #include <algorithm>
@@ -200,70 +202,99 @@ __global__ void interp_dir_kernel(const double* __restrict__ in, double* __restr
     }
 }
 
-// ---------------------------------------------------------------- a5: surrogate evaluation
-template <int DIM>
-__global__ void eval_kernel(const double* __restrict__ coef, int ns, const int* __restrict__ espan,
-                            const double* __restrict__ evals, int q, int L, int lo, int m, int p,
-                            int t_first, int field_base, double* __restrict__ fields, long long pitch) {
-    const int t = t_first + blockIdx.y;
-    const int f = t - field_base;
-    const int PP = 2 * p + 1;
-    int delta[3] = {0, 0, 0};
-    {
-        int tt = t;
-        for (int k = 0; k < DIM; ++k) {
-            delta[k] = tt % PP - p;
-            tt /= PP;
+// ---------------------------------------------------------------- a5: sum-factorised evaluation
+// The surrogate value at interior row l = (l_0, .., l_{d-1}) is the tensor B-spline
+// sum_{a} C[espan(l_k) + a_k]_k prod_k evals[l_k][a_k].  Every row of Omega~ is a
+// tensor-grid point, so the sum is contracted one direction at a time over the whole
+// grid: direction k turns the coefficient index (extent ns) into the row index
+// (extent L), (q+1) FMAs per output value.  In 3-D this is ns^2 L + ns L^2 + L^3 values
+// per field ((q+1) FMAs each) instead of L^3 ((q+1)^3 + (q+1)^2 + (q+1)) row by row:
+// about 11x fewer FP64 FMAs at ns = 16, L = 90, q = 2.
+//
+// eval_dir_kernel: directions 0..d-2.  Tensor layout colex (direction 0 fastest),
+// extents L for directions < dir, ns for directions >= dir on input; output has
+// extent L in direction dir too.  Fields are contiguous blocks of in_stride / out
+// values.
+__global__ void eval_dir_kernel(const double* __restrict__ in, long long in_stride, double* __restrict__ out,
+                                long long out_per_field, int nf, const int* __restrict__ espan,
+                                const double* __restrict__ evals, int q, int ns, int L, int dim, int dir) {
+    const long long total = (long long)nf * out_per_field;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(idx / out_per_field);
+        long long r = idx % out_per_field;
+        long long in_off = 0, in_mul = 1;
+        int l = 0;
+        long long dir_mul = 1;
+        for (int k = 0; k < dim; ++k) {
+            const int ext_out = k <= dir ? L : ns;
+            const int ext_in = k < dir ? L : ns;
+            const int ik = (int)(r % ext_out);
+            r /= ext_out;
+            if (k == dir) {
+                l = ik;
+                dir_mul = in_mul;
+            } else {
+                in_off += ik * in_mul;
+            }
+            in_mul *= ext_in;
         }
-    }
-    int nsd = ns, Ld = L;
-    for (int k = 1; k < DIM; ++k) {
-        nsd *= ns;
-        Ld *= L;
-    }
-    const double* C = coef + (size_t)t * nsd;
-    const int q1 = q + 1;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < Ld; r += gridDim.x * blockDim.x) {
-        int l[3] = {0, 0, 0};
-        decode<DIM>(r, L, l);
-        bool ok = true;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-            const int j = l[k] + delta[k];
-            ok = ok && j >= 0 && j < L;
-        }
-        if (!ok) continue;                    // neighbour outside Omega~: true entry from the band
+        const double* src = in + (size_t)f * in_stride + in_off + (long long)espan[l] * dir_mul;
+        const double* e = evals + (size_t)l * (q + 1);
         double acc = 0.0;
-        if (DIM == 2) {
-            const int s0 = espan[l[0]], s1 = espan[l[1]];
-            const double* e0 = evals + (size_t)l[0] * q1;
-            const double* e1 = evals + (size_t)l[1] * q1;
-            for (int b = 0; b < q1; ++b) {
-                double row = 0.0;
-                for (int a = 0; a < q1; ++a) row += C[(size_t)(s1 + b) * ns + s0 + a] * e0[a];
-                acc += row * e1[b];
-            }
-        } else {
-            const int s0 = espan[l[0]], s1 = espan[l[1]], s2 = espan[l[2]];
-            const double* e0 = evals + (size_t)l[0] * q1;
-            const double* e1 = evals + (size_t)l[1] * q1;
-            const double* e2 = evals + (size_t)l[2] * q1;
-            for (int c = 0; c < q1; ++c) {
-                double plane = 0.0;
-                for (int b = 0; b < q1; ++b) {
-                    double row = 0.0;
-                    for (int a = 0; a < q1; ++a)
-                        row += C[((size_t)(s2 + c) * ns + s1 + b) * ns + s0 + a] * e0[a];
-                    plane += row * e1[b];
-                }
-                acc += plane * e2[c];
-            }
-        }
-        long long li = 0;
-        for (int k = DIM - 1; k >= 0; --k) li = li * m + (lo + l[k]);
-        fields[(size_t)f * pitch + li] = acc;
+        for (int a = 0; a <= q; ++a) acc += src[(long long)a * dir_mul] * e[a];
+        out[idx] = acc;
     }
 }
+
+// Last direction (d-1) straight into the field slots: K~_delta(x~_i) / M~_delta(x~_i)
+// at every interior row whose neighbour i + delta is interior (the other slots hold
+// the band's true entries).  Input extents: L in directions < d-1, ns in d-1.
+template <int DIM>
+__global__ void eval_last_kernel(const double* __restrict__ in, long long in_stride, int nf, int t_first,
+                                 int field_base, const int* __restrict__ espan, const double* __restrict__ evals,
+                                 int q, int ns, int L, int lo, int m, int p, double* __restrict__ fields,
+                                 long long pitch) {
+    long long Ld = L;
+    for (int k = 1; k < DIM; ++k) Ld *= L;
+    const long long total = (long long)nf * Ld;
+    const int PP = 2 * p + 1;
+    const long long plane = Ld / L;   // L^{d-1}: stride of direction d-1 in the input
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(idx / Ld);
+        const long long r = idx % Ld;
+        const int t = t_first + f;
+        int l[3] = {0, 0, 0};
+        {
+            long long rr = r;
+            for (int k = 0; k < DIM; ++k) {
+                l[k] = (int)(rr % L);
+                rr /= L;
+            }
+        }
+        bool ok = true;
+        {
+            int tt = t;
+            for (int k = 0; k < DIM; ++k) {
+                const int j = l[k] + (tt % PP - p);
+                tt /= PP;
+                ok = ok && j >= 0 && j < L;
+            }
+        }
+        if (!ok) continue;   // neighbour outside Omega~: true entry from the band
+        const int ll = l[DIM - 1];
+        const long long low = r - (long long)ll * plane;   // index of the lower directions
+        const double* src = in + (size_t)f * in_stride + low + (long long)espan[ll] * plane;
+        const double* e = evals + (size_t)ll * (q + 1);
+        double acc = 0.0;
+        for (int a = 0; a <= q; ++a) acc += src[(long long)a * plane] * e[a];
+        long long li = 0;
+        for (int k = DIM - 1; k >= 0; --k) li = li * m + (lo + l[k]);
+        fields[(size_t)(t - field_base) * pitch + li] = acc;
+    }
+}
+
 
 // ---------------------------------------------------------------- volume-preserving mass
 // Sec. 3.4 (remark on volume preservation): M~ = D + M~_0 with D_ii = int phi_i
@@ -633,24 +664,52 @@ extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigne
             }
         }
         cudaEventRecord(tm.ev[3], st);
-        // ---- a5: surrogate values in Omega~
+        // ---- a5: surrogate values in Omega~, sum-factorised (one direction per launch),
+        // fields in chunks so that the intermediate tensors stay below ~256 MB
         long long Ld = 1;
         for (int k = 0; k < dim; ++k) Ld *= L;
-        const int gx = (int)std::min<long long>((Ld + 255) / 256, 2048);
+        // values per field after contracting directions 0..k: L^{k+1} ns^{d-1-k}
+        std::vector<long long> ext(dim);
+        for (int k = 0; k < dim; ++k) {
+            long long v = 1;
+            for (int j = 0; j < dim; ++j) v *= j <= k ? L : ns;
+            ext[k] = v;
+        }
+        long long per_field = 0;
+        for (int k = 0; k + 1 < dim; ++k) per_field += ext[k];
+        const int chunk = (int)std::max<long long>(1, std::min<long long>(D, (32LL << 20) / std::max(1LL, per_field)));
+        DevBuf d_eval;
+        if ((rc = d_eval.alloc(sizeof(double) * std::max(1LL, per_field) * chunk))) return bail(rc);
         for (int which = 0; which < 2; ++which) {
-            const int t_first = which ? T0 : T0 + 1;
-            const int cnt = D - t_first;
+            const int t_begin = which ? T0 : T0 + 1;
             const int fbase = which ? T0 : T0 + 1;
-            dim3 grid(gx, cnt);
             double* coef = which ? ops->cM.as<double>() : ops->cK.as<double>();
             double* fld = which ? ops->fM64.as<double>() : ops->fK64.as<double>();
-            if (dim == 2)
-                eval_kernel<2><<<grid, 256, 0, st>>>(coef, ns, d_espan.as<int>(), d_evals.as<double>(), q, L,
-                                                     2 * p, m, p, t_first, fbase, fld, pitch);
-            else
-                eval_kernel<3><<<grid, 256, 0, st>>>(coef, ns, d_espan.as<int>(), d_evals.as<double>(), q, L,
-                                                     2 * p, m, p, t_first, fbase, fld, pitch);
-            IGA_LAUNCH_CHECK("eval_kernel");
+            for (int t0c = t_begin; t0c < D; t0c += chunk) {
+                const int nf = std::min(chunk, D - t0c);
+                const double* in = coef + (size_t)t0c * nsd;
+                long long in_stride = nsd;
+                double* buf = d_eval.as<double>();
+                for (int dir = 0; dir + 1 < dim; ++dir) {
+                    const long long total = (long long)nf * ext[dir];
+                    const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+                    eval_dir_kernel<<<grid, 256, 0, st>>>(in, in_stride, buf, ext[dir], nf, d_espan.as<int>(),
+                                                          d_evals.as<double>(), q, ns, L, dim, dir);
+                    IGA_LAUNCH_CHECK("eval_dir_kernel");
+                    in = buf;
+                    in_stride = ext[dir];
+                    buf += (size_t)nf * ext[dir];
+                }
+                const long long total = (long long)nf * Ld;
+                const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+                if (dim == 2)
+                    eval_last_kernel<2><<<grid, 256, 0, st>>>(in, in_stride, nf, t0c, fbase, d_espan.as<int>(),
+                                                              d_evals.as<double>(), q, ns, L, 2 * p, m, p, fld, pitch);
+                else
+                    eval_last_kernel<3><<<grid, 256, 0, st>>>(in, in_stride, nf, t0c, fbase, d_espan.as<int>(),
+                                                              d_evals.as<double>(), q, ns, L, 2 * p, m, p, fld, pitch);
+                IGA_LAUNCH_CHECK("eval_last_kernel");
+            }
         }
     } else {
         cudaEventRecord(tm.ev[2], st);
