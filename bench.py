@@ -265,15 +265,7 @@ def run_ours(args, rank, world, device):
         "metric": METRIC, "value": value, "unit": "shot-steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "dim": w["dim"], "p": w["p"], "n_el": w["n_el"], "N": N,
-                   "q": w["q"], "M": w["M"], "nsteps": nsteps, "nshot": args.nshot, "cg_rtol": args.cg_rtol,
-                   "cg_schedule": args.solve,
-                   "cg_start": ("previous acceleration" if args.cg_guess == 0 else
-                                "polynomial extrapolation in time, order %d" % args.cg_guess),
-                   "precision": "FP32 fields/vectors/apply, FP64 quadrature, residual and dot products",
-                   "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (
-                       (oinfo.nK + oinfo.nM) * oinfo.pitch * 12 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(args, world),
         "components": comps,
         "roofline": {"bound": "hbm",
                      "kernel": ("pcg graph (cgg_phase1_kernel + cgg_phase2_kernel)" if args.solve == "graph"
@@ -653,6 +645,26 @@ def oracle_sample(args):
             "surrogate_rows_per_s": N / asm_s, "sample_seconds": sample_s}
 
 
+def workload_config(args, world=1):
+    """The `config` object of both arms: the workload and the settings of the timed pass
+    (host-side arithmetic only)."""
+    from paper_2004_05197_gb300 import workloads as W
+    w = W.scaled(args.workload)
+    nsteps = args.nsteps or w["steps"]
+    m = w["n_el"] + w["p"]
+    N = m ** w["dim"]
+    D = (2 * w["p"] + 1) ** w["dim"]
+    pitch = (N + 63) // 64 * 64
+    return {"workload": args.workload, "dim": w["dim"], "p": w["p"], "n_el": w["n_el"], "N": N,
+            "q": w["q"], "M": w["M"], "nsteps": nsteps, "nshot": args.nshot, "cg_rtol": args.cg_rtol,
+            "cg_schedule": args.solve,
+            "cg_start": ("previous acceleration" if args.cg_guess == 0 else
+                         "polynomial extrapolation in time, order %d" % args.cg_guess),
+            "precision": "FP32 fields/vectors/apply, FP64 quadrature and residual, compensated dot products",
+            "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (D * pitch * 12 / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, one bounded sample per step."""
     for _ in range(args.warmup):
@@ -667,7 +679,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "shot-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
+            "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": v, "unit": "shot-steps/s", "cores": 1, "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": v, "unit": "shot-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
