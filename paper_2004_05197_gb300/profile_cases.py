@@ -1,11 +1,13 @@
-"""Small profiling cases for ncu: K~ applies and fixed-iteration PCG solves.
+"""Small profiling cases for ncu.
 
     python -m paper_2004_05197_gb300.profile_cases [n_el]
+    python -m paper_2004_05197_gb300.profile_cases assemble [n_el]
 
 Workload: the cube96_p2 family at n_el (default 80: the FP32 fields exceed L2).
-Launch order: two K~ applies, then persistent PCG solves of exactly 10, 10 and 20
-iterations (rtol 0), so that a capture of the last two separates the per-solve
-and per-iteration DRAM traffic.
+Default case, launch order: two K~ applies, then persistent PCG solves of exactly
+10, 10 and 20 iterations (rtol 0), so that a capture of the last two separates the
+per-solve and per-iteration DRAM traffic.  `assemble`: one surrogate assembly of
+the space (band quadrature, sample rows, interpolation, evaluation).
 """
 import sys
 
@@ -32,5 +34,16 @@ def main(n_el=80):
     print("ok N", N)
 
 
+def assemble(n_el=40):
+    w = W.scaled("cube96_p2", n_el=n_el)
+    sp = W.make_space(w)
+    ops = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
+    torch.cuda.synchronize()
+    print("ok N", iga.iga_ops_info_get(ops).N, "band ms", iga.iga_ops_info_get(ops).t_band_ms)
+
+
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 80)
+    if len(sys.argv) > 1 and sys.argv[1] == "assemble":
+        assemble(int(sys.argv[2]) if len(sys.argv) > 2 else 40)
+    else:
+        main(int(sys.argv[1]) if len(sys.argv) > 1 else 80)
