@@ -19,7 +19,12 @@ waves", arXiv:2004.05197) in the paper's order and notation:
                    surrogate matrices (Eq. DefinitionOfSurrogateMatrixSymmetric,
                    Eq. DefinitionOfSurrogateMatrixSymmetricKernel)
 * ``wave``       - Jacobi-preconditioned CG on the consistent mass and leapfrog
-                   time stepping of M u'' + K u = f (Sec. 4.6 context)
+                   time stepping of M u'' + K u = f (Sec. 4.6 context); the CG start
+                   of each step (polynomial extrapolation in time, ``cg_start``)
+* ``adjoint``    - receiver misfit and its tangent-linear directional derivative
+                   with respect to the wave speed's B-spline coefficients
+* ``multipatch`` - several patches glued along sides with a first-visit global
+                   numbering (Sec. 3.2 / 3.4 multi-patch remarks)
 
 Every routine is deliberately slow and unblocked; numpy / scipy routines are used
 only as library primitives (dense solves, sparse mat-vecs, eigensolvers).
