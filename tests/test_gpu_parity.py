@@ -400,6 +400,47 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     assert err <= tol and terr <= tol
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_multishot_wave_with_extrapolated_start_matches_single_shots(dtype):
+    """Five shots in one wave (CG chunks of 4 + 1 right-hand sides) with the order-3 CG
+    start: every shot equals the same shot stepped alone (FP64 1e-11: both solve to
+    1e-13; FP32 2e-5: the chunks reduce in a different order and stop at different
+    iterates within rtol 1e-6)."""
+    name = "annulus40_p3_sincos"
+    w = CASES[name]()
+    _, ops = gpu_ops(name)
+    N = iga.iga_ops_info_get(ops).N
+    dt = W.dt_of(w)
+    src = inputs.shot_positions(5, dim=2, seed=inputs.SEED_SHOTS_2D + 7)
+    dt_code = iga.IGA_F64 if dtype == "f64" else iga.IGA_F32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    rtol = 1e-13 if dtype == "f64" else 1e-6
+    nsteps = 25
+
+    def run(pos):
+        wv = iga.iga_wave_create(ops, len(pos), dt_code, dt, src_pos=pos, f0=10.0, t0=0.1, cg_rtol=rtol,
+                                 cg_max_it=3000, cg_guess=3)
+        iga.iga_wave_step(wv, nsteps)
+        u = torch.empty((len(pos), N), dtype=tdt, device="cuda")
+        iga.iga_wave_get_state(wv, u)
+        torch.cuda.synchronize()
+        iga.iga_wave_destroy(wv)
+        return u.double().cpu().numpy()
+
+    multi = run(src)
+    tol = 1e-11 if dtype == "f64" else 2e-5
+    for k in range(5):
+        single = run(src[k:k + 1])[0]
+        assert np.linalg.norm(multi[k] - single) <= tol * np.linalg.norm(single), k
+
+
+def test_wave_rejects_cg_guess_out_of_range():
+    _, ops = gpu_ops("annulus64_p2")
+    for bad in (-1, 7):
+        with pytest.raises(iga.IgaError):
+            iga.iga_wave_create(ops, 1, iga.IGA_F64, 1e-3, cg_guess=bad)
+
+
 @pytest.mark.parametrize("case", ["annulus40", "cube16_M6"])
 def test_spectrum_extremes_match_dense_eigensolver(case):
     """Lanczos (K~, M~) extremes vs scipy's dense generalized symmetric eigensolver."""
