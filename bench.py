@@ -317,6 +317,98 @@ def stencil_apply_leg(ctx, args):
     return res
 
 
+def _time_us(fn, stream, reps=20, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
+def next_rows_leg(ctx, args):
+    """--next-rows: measurements of the rows beyond the hot path.  (1) The
+    volume-preserving mass M~ = D + M~_0 on the bench operator: assembly time, FP32 apply
+    and FP32 Jacobi-PCG (rtol 1e-6, zero start) against the plain surrogate mass.
+    (2) Multi-patch: the quarter annulus as four angular sector patches (p = 3, 256^2
+    elements each, q = 3, M = 8, glued along three sides), global FP32 / FP64 applies and
+    the FP32 mass solve, against one 256^2 patch."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2004_05197_gb300 import iga
+    space, ops, wave, w, nsteps, dt, src, rec = ctx
+    stream = torch.cuda.current_stream()
+    out = {}
+    # (1) volume-preserving mass on the bench space
+    vp = iga.iga_surrogate_assemble(space, w["p"], w["q"], w["M"], iga.IGA_MASS_VOLUME_PRESERVING, stream)
+    torch.cuda.synchronize()
+    N = iga.iga_ops_info_get(ops).N
+    b = torch.tensor(inputs.vectors(N, 1), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(b)
+    for name, o in (("plain", ops), ("volume_preserving", vp)):
+        info = iga.iga_ops_info_get(o)
+        t_apply = _time_us(lambda: iga.iga_stencil_apply(o, iga.IGA_OP_M, iga.IGA_F32, b, y, 1, stream), stream)
+        a = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it, rel = iga.iga_mass_solve(o, iga.IGA_F32, b, a, 1, 1e-6, 2000, stream=stream,
+                                        allow_not_converged=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["mass_" + name] = {"assembly_ms": info.t_total_ms, "apply_fp32_us": t_apply,
+                               "apply_gbs": (info.nM * 4 + 8) * N / (t_apply * 1e-6) / 1e9,
+                               "solve_fp32_iterations": int(it[0]), "solve_fp32_ms": e0.elapsed_time(e1),
+                               "solve_fp32_relres": float(rel[0])}
+    iga.iga_ops_destroy(vp)
+    # (2) multi-patch quarter annulus, four sectors
+    p, n_el, q, M = 3, 256, 3, 8
+    e = np.linspace(0.0, 0.5 * np.pi, 5)
+    sectors = [(1.0, 2.0, e[l], e[l + 1]) for l in range(4)]
+    ifs = [(l, 3, l + 1, 2, 0) for l in range(3)]
+    spaces = [iga.iga_space_create(2, p, n_el, iga.IGA_MAP_ANNULUS_SECTOR, 0.0, iga.IGA_COEF_CONST, 1.0, sector=sc)
+              for sc in sectors]
+    pops = [iga.iga_surrogate_assemble(sp, p, q, M, 0, stream) for sp in spaces]
+    mp = iga.iga_multipatch_create(pops, ifs)
+    G = iga.iga_multipatch_size(mp)
+    n_loc = iga.iga_ops_info_get(pops[0]).N
+    res = {"patches": 4, "p": p, "n_el_per_patch": n_el, "global_functions": G}
+    for dtype, tdt, tag in ((iga.IGA_F32, torch.float32, "fp32"), (iga.IGA_F64, torch.float64, "fp64")):
+        xg = torch.tensor(inputs.vectors(G, 1), dtype=tdt, device="cuda")
+        yg = torch.empty_like(xg)
+        xl = torch.tensor(inputs.vectors(n_loc, 1), dtype=tdt, device="cuda")
+        yl = torch.empty_like(xl)
+        for which, wn in ((iga.IGA_OP_K, "K"), (iga.IGA_OP_M, "M")):
+            res["apply_%s_%s_us" % (wn, tag)] = _time_us(
+                lambda: iga.iga_multipatch_apply(mp, which, dtype, xg, yg, 1, stream), stream)
+            res["single_patch_apply_%s_%s_us" % (wn, tag)] = _time_us(
+                lambda: iga.iga_stencil_apply(pops[0], which, dtype, xl, yl, 1, stream), stream)
+    bg = torch.tensor(inputs.vectors(G, 1), dtype=torch.float32, device="cuda")
+    ag = torch.zeros_like(bg)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, it, rel = iga.iga_multipatch_mass_solve(mp, iga.IGA_F32, bg, ag, 1, 1e-6, 2000, stream=stream,
+                                               allow_not_converged=True)
+    torch.cuda.synchronize()
+    res["mass_solve_fp32_iterations"] = int(it[0])
+    res["mass_solve_fp32_ms"] = (time.perf_counter() - t) * 1e3
+    res["mass_solve_fp32_relres"] = float(rel[0])
+    iga.iga_multipatch_destroy(mp)
+    for o in pops:
+        iga.iga_ops_destroy(o)
+    for sp in spaces:
+        iga.iga_space_destroy(sp)
+    out["multipatch"] = res
+    return {"next_rows": out}
+
+
 def fp64_plain_and_error(ctx, args):
     """FP64 plain single-shot schedule on the same workload (bounded steps) and the FP32 error."""
     import numpy as np
@@ -713,6 +805,8 @@ def main():
     ap.add_argument("--batched-cg-guess", type=int, default=3, choices=range(7),
                     help="CG start order of the batched leg and of its plain FP64 comparison")
     ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--next-rows", action="store_true",
+                    help="also measure the volume-preserving mass and the multi-patch operators")
     ap.add_argument("--adjoint", action="store_true",
                     help="also run the adjoint-gradient leg (several minutes: FP64 forward / reverse sweeps)")
     ap.add_argument("--adjoint-steps", type=int, default=600)
@@ -736,6 +830,8 @@ def main():
     out, ctx = run_ours(args, rank, world, device)
     if rank == 0:
         out["components"].update(stencil_apply_leg(ctx, args))
+        if args.next_rows:
+            out["components"].update(next_rows_leg(ctx, args))
         if not args.no_compare:
             out["components"].update(fp64_plain_and_error(ctx, args))
         if args.e2e_steps > 0:
