@@ -29,3 +29,16 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": "shot-steps/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_pcg_algorithmic_bytes_match_the_documented_count():
+    """Roofline numerator of the persistent PCG: 536 B per row and launch (two 63-field
+    FP32 applies + vectors) and 316 B per row and iteration on the 3-D p = 2 operator;
+    the FP64 path doubles field and vector bytes (the residual is FP64 in both)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.cg_bytes(63, 1, 4) == (536, 316)
+    assert bench.cg_bytes(63, 1, 8) == (2 * 63 * 8 + 8 + 48, 63 * 8 + 8 + 104)
+    # R right-hand sides share the field stream
+    init4, it4 = bench.cg_bytes(63, 4, 4)
+    assert it4 - 63 * 4 - 4 == 4 * (316 - 63 * 4 - 4)
