@@ -196,6 +196,29 @@ int iga_ops_sample_indices(const iga_ops* ops, int* host_dst);
 int iga_stencil_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y,
                       int nrhs, void* stream);
 
+/* Which kernels run the FP32 operators of a 3-D ops (stencil_apply and the
+ * persistent mass solve; FP64 and 2-D operators always use the row kernels).
+ *   IGA_PATH_AUTO  (default) the brick kernels where a brick form exists and its
+ *                  bricks are large enough to be faster (about 3,000 rows per
+ *                  brick for M~, 5,000 for K~), else the row kernels
+ *   IGA_PATH_ROWS  one thread per row, fields read from the colex SoA layout
+ *   IGA_PATH_BRICK the brick kernels (IGA_ERR_ARG if the ops has no brick form)
+ * Brick form (built by surrogate_assemble for dim 3, p <= 2): the rows are cut
+ * into about one brick per SM; each CTA streams its brick's fields through a
+ * TMA ring of shared-memory stages from a second, padded and group-ordered copy
+ * of the FP32 fields (about 1.06x the colex FP32 fields), so every field and
+ * vector value a row needs is read from shared memory (Sec. 3.3: matrix-free use
+ * of the stored stencil data).  Results equal the row kernels' up to the FP32
+ * summation order.  Host-only, synchronous. */
+#define IGA_PATH_AUTO  0
+#define IGA_PATH_ROWS  1
+#define IGA_PATH_BRICK 2
+int iga_ops_set_path(iga_ops* ops, int path);
+/* Brick plan of an ops (all outputs nullable host pointers; zeros without a
+ * brick form): bricks (= CTAs of a brick launch), threads per CTA, ring
+ * stages, dynamic shared memory bytes per CTA.  Host-only. */
+int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stages, int* smem_bytes);
+
 /* mass_solve: Jacobi-PCG on M~ a = b for nrhs right-hand sides (device
  * pointers [nrhs][N] of `dtype`; x holds the initial guess on entry and the
  * solution on exit).  Stops each RHS when ||r||_2 <= rtol ||b||_2 (rtol = 0:

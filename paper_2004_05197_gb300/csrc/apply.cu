@@ -144,6 +144,15 @@ int launch_apply(const iga_ops* ops, int which, int dtype, const void* x, void* 
         const double* F = which == IGA_OP_K ? ops->fK64.as<double>() : ops->fM64.as<double>();
         return apply_dispatch<double>(ops, which, F, (const double*)x, (double*)y, nrhs, st);
     }
+    if (brick_usable(ops, which)) {
+        // brick kernels: one launch per right-hand side
+        const long long N = ops->N;
+        for (int r = 0; r < nrhs; ++r) {
+            const int rc = brick_apply(ops, which, (const float*)x + (size_t)r * N, (float*)y + (size_t)r * N, st);
+            if (rc) return rc;
+        }
+        return IGA_OK;
+    }
     const float* F = which == IGA_OP_K ? ops->fK32.as<float>() : ops->fM32.as<float>();
     return apply_dispatch<float>(ops, which, F, (const float*)x, (float*)y, nrhs, st);
 }

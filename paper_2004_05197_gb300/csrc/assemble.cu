@@ -753,6 +753,8 @@ extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigne
     ops->t_eval = t;
     cudaEventElapsedTime(&t, tm.ev[0], tm.ev[5]);
     ops->t_total = t;
+    rc = brick_prepare(ops, st);
+    if (rc) return bail(rc);
     if (!(flags & IGA_KEEP_SAMPLES)) {
         ops->sK.release();
         ops->sM.release();

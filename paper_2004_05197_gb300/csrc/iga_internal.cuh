@@ -2,9 +2,11 @@
 // Everything here is private to libiga; the public ABI is include/iga.h.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (a type only: the driver call is reached through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -63,6 +65,28 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// Brick form of the 3-D FP32 operators (brick.cu).  A brick is a box of rows
+// x0 + [0, nx) x y0 + [0, ny) x z0 + [0, nz); cls selects its tensor-map box.
+struct BrickDesc {
+    int x0, y0, z0, nx, ny, nz, cls, warps;
+};
+constexpr int kBrickMaxCls = 12;
+struct alignas(64) BrickMaps {
+    CUtensorMap tm[kBrickMaxCls];   // one box shape per class, all over the same padded field copy
+    int bx[kBrickMaxCls], by[kBrickMaxCls], bz[kBrickMaxCls];
+};
+struct BrickOps {
+    int P = 0, m = 0, XP = 0, ncw = 0, ns = 0, nbricks = 0, ncls = 0, bzm = 0;
+    long long fsz = 0;                  // elements of one padded field (XP * m * m)
+    int stage_floats = 0, xt_floats = 0;
+    size_t smem = 0;                    // dynamic shared memory of the brick kernels
+    std::vector<BrickDesc> host;
+    DevBuf bricks;                      // [nbricks] BrickDesc
+    DevBuf fK, fM;                      // padded, group-ordered FP32 fields
+    DevBuf err;                         // device error word of the brick kernels (bit 16: a wait timed out)
+    BrickMaps mapK, mapM;
+};
+
 }  // namespace iga
 
 struct iga_space {
@@ -94,6 +118,8 @@ struct iga_ops {
     iga::DevBuf sK, sM, cK, cM;              // samples / coefficients [D][ns^dim]
     iga::DevBuf status;                      // int flags: [0] nonfinite
     iga::DevBuf work;                        // CG workspace of mass_solve (grown on demand)
+    std::unique_ptr<iga::BrickOps> brick;    // brick form of the FP32 fields (3-D), else null
+    int path = 0;                            // IGA_PATH_*: which kernels apply the FP32 operators
     int n_band, n_samples;
     float t_sample, t_band, t_interp, t_eval, t_total;
 };
@@ -122,6 +148,10 @@ int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long 
                     int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st,
                     void* work, size_t work_bytes, long long* iter_acc, int* status_acc);
 size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs);
+// brick.cu: builds ops->brick (3-D, FP32 fields present); no-op otherwise
+int brick_prepare(iga_ops* ops, cudaStream_t st);
+bool brick_usable(const iga_ops* ops, int which);
+int brick_apply(const iga_ops* ops, int which, const float* x, float* y, cudaStream_t st);
 int spectrum_impl(const iga_ops* ops, int dtype, int k, double* lam_min, double* lam_max, cudaStream_t st);
 int wave_step_impl(iga_wave* w, int nsteps, cudaStream_t st);
 int wave_initial_state(iga_wave* w, cudaStream_t st);

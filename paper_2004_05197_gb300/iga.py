@@ -29,6 +29,7 @@ IGA_OP_K, IGA_OP_M = 0, 1
 IGA_TRUE_ONLY, IGA_KEEP_SAMPLES, IGA_MASS_VOLUME_PRESERVING = 1, 2, 4
 IGA_SOLVE_PLAIN, IGA_SOLVE_GRAPH = 1, 2
 IGA_INIT_ZERO, IGA_INIT_GAUSS_PULSE = 0, 1
+IGA_PATH_AUTO, IGA_PATH_ROWS, IGA_PATH_BRICK = 0, 1, 2
 
 EXPORTED = [
     "iga_space_create", "iga_space_destroy", "iga_space_info_get", "iga_surrogate_assemble",
@@ -40,7 +41,7 @@ EXPORTED = [
     "iga_batch_create", "iga_batch_destroy", "iga_batch_step", "iga_batch_tune", "iga_batch_partition",
     "iga_mass_solve_noalloc", "iga_sampling_length_for_mesh",
     "iga_multipatch_create", "iga_multipatch_destroy", "iga_multipatch_size", "iga_multipatch_global_index",
-    "iga_multipatch_apply", "iga_multipatch_mass_solve",
+    "iga_multipatch_apply", "iga_multipatch_mass_solve", "iga_ops_set_path", "iga_ops_brick_info",
 ]
 
 
@@ -104,6 +105,8 @@ _sig = {
     "iga_ops_copy_samples": [_vp, _i, _vp, _vp],
     "iga_ops_sample_indices": [_vp, C.POINTER(_i)],
     "iga_stencil_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
+    "iga_ops_set_path": [_vp, _i],
+    "iga_ops_brick_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "iga_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_multipatch_create": [_i, C.POINTER(_vp), _i, C.POINTER(iga_interface), C.POINTER(_vp)],
     "iga_multipatch_destroy": [_vp],
@@ -240,6 +243,17 @@ def iga_sampling_length_for_mesh(h, p, q, a=0.0, b=0.0, C_=1.0, eps=0.1):
 # ---- operators -----------------------------------------------------------------
 def iga_stencil_apply(ops, which, dtype, x, y, nrhs, stream=None):
     _check(_lib.iga_stencil_apply(ops, which, dtype, _dptr(x), _dptr(y), nrhs, _stream(stream)))
+
+
+def iga_ops_set_path(ops, path):
+    _check(_lib.iga_ops_set_path(ops, path))
+
+
+def iga_ops_brick_info(ops):
+    """(bricks, threads per CTA, ring stages, shared-memory bytes per CTA); zeros without a brick form."""
+    v = [C.c_int() for _ in range(4)]
+    _check(_lib.iga_ops_brick_info(ops, *[C.byref(t) for t in v]))
+    return tuple(t.value for t in v)
 
 
 def iga_mass_solve(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_stats=True, stream=None,
