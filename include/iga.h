@@ -226,9 +226,13 @@ int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stag
  * residual and dot products.  Default schedule: one persistent cooperative
  * launch for all iterations with device-side convergence; IGA_SOLVE_PLAIN:
  * one launch per phase and a host convergence test per iteration.
- * iters_out / relres_out: host arrays of nrhs (nullable); writing them
- * synchronises the stream.  Returns IGA_ERR_NOT_CONVERGED if some RHS
- * missed rtol (x still holds the last iterate). */
+ * FP32 3-D operators with a brick form (see iga_ops_set_path) run the brick
+ * form of the persistent launch for single right-hand sides.
+ * iters_out / relres_out: host arrays of nrhs (nullable).  The call always
+ * synchronises the stream and reads the solver status back, also when both are
+ * NULL.  Returns IGA_ERR_NOT_CONVERGED if some RHS missed rtol (x still holds
+ * the last iterate), IGA_ERR_NONFINITE on a CG breakdown, IGA_ERR_TIMEOUT if a
+ * bounded device-side wait (grid barrier, field ring) gave up. */
 int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs,
                    double rtol, int max_it, unsigned flags, int* iters_out,
                    double* relres_out, void* stream);
@@ -247,9 +251,15 @@ int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nr
  * about 40 N bytes for FP64 with nrhs < 4 and 160 N with nrhs >= 4 (FP32:
  * 24 N and 96 N), plus ~100 KB; e.g. FP64 single-RHS solves up to about
  * 1.6 M rows.  Larger requests return IGA_ERR_ARG before any work.
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, which may load the module holding it) with that
- * device current; make that first call before any stream capture.
+ * Set-up: every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device may load the
+ * module that holds the array, so make that first call before any stream
+ * capture.  With lazy module loading (the CUDA default) only devices on which
+ * this entry point runs hold the array; with CUDA_MODULE_LOADING=EAGER every
+ * device that loads the library does.  The call synchronises the stream (the
+ * solver status is always read back into host memory).
+ * IGA_SOLVE_GRAPH is rejected (IGA_ERR_ARG): that schedule instantiates a CUDA
+ * graph per call, which may reserve device resources.
  * Sharing: all calls on a device use the same array, so calls that overlap in
  * time (different streams or host threads) race and corrupt one another;
  * the caller must serialise them (e.g. one stream). */

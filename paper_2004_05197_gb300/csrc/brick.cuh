@@ -159,24 +159,45 @@ __device__ __forceinline__ BrickGeo brick_geo(const BrickMaps& maps, const Brick
 
 // Vector tile of the brick grown by P on every side ([z][y][x], row pitch bxb,
 // plane byb * bxb), zero outside the grid.  Called by the consumer warps only;
-// ends with their named barrier.  COHERENT: plain loads (vectors written earlier
-// in the same persistent launch), else read-only loads.
+// ends with their named barrier.  Each warp loads eight tile rows (two values per
+// lane and row) before it stores any, so a tile costs about two L2 round trips
+// instead of one per row.  COHERENT: plain loads (vectors written earlier in the
+// same persistent launch), else read-only loads.
 template <int P, bool COHERENT>
 __device__ __forceinline__ void brick_load_tile(float* xt, const float* x, const BrickGeo& g, int m, int cwarp,
                                                 int ncw, int lane) {
+    constexpr int U = 8;
     const int zt = g.nz + 2 * P, rows = g.byb * zt;
     const long long mm = (long long)m * m;
-    for (int r = cwarp; r < rows; r += ncw) {
-        const int yi = r % g.byb, zi = r / g.byb;
-        const int yy = g.y0 - P + yi, zz = g.z0 - P + zi;
-        const bool rowok = yy >= 0 && yy < m && zz >= 0 && zz < m;
-        const float* src = x + zz * mm + (long long)yy * m;
-        float* dst = xt + (size_t)r * g.bxb;
-        for (int xi = lane; xi < g.bxb; xi += 32) {
-            const int xx = g.x0 - P + xi;
-            float v = 0.f;
-            if (rowok && xx >= 0 && xx < m) v = COHERENT ? src[xx] : __ldg(src + xx);
-            dst[xi] = v;
+    for (int xc = 0; xc < g.bxb; xc += 64)   // one pass for boxes up to 64 columns
+    for (int r0 = cwarp; r0 < rows; r0 += U * ncw) {
+        const int ia = xc + lane, ib = ia + 32;
+        const int xa = g.x0 - P + ia, xb = xa + 32;
+        const bool oka = ia < g.bxb && xa >= 0 && xa < m;
+        const bool okb = ib < g.bxb && xb >= 0 && xb < m;
+        float va[U], vb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = r0 + u * ncw;
+            va[u] = 0.f;
+            vb[u] = 0.f;
+            if (r < rows) {
+                const int yy = g.y0 - P + r % g.byb, zz = g.z0 - P + r / g.byb;
+                if (yy >= 0 && yy < m && zz >= 0 && zz < m) {
+                    const float* src = x + zz * mm + (long long)yy * m;
+                    if (oka) va[u] = COHERENT ? src[xa] : __ldg(src + xa);
+                    if (okb) vb[u] = COHERENT ? src[xb] : __ldg(src + xb);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = r0 + u * ncw;
+            if (r < rows) {
+                float* dst = xt + (size_t)r * g.bxb;
+                if (ia < g.bxb) dst[ia] = va[u];
+                if (ib < g.bxb) dst[ib] = vb[u];
+            }
         }
     }
     named_bar_sync(1, ncw * 32);

@@ -30,9 +30,10 @@ __device__ __forceinline__ void block_sum(double* v, double* wsum /*[kWarps][K]*
 }
 
 // Bounded barrier over `nblocks` co-resident blocks (a whole cooperative grid or
-// one partition of it).  On time-out it sets bit 4 of *err and returns false;
-// every caller then leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks) {
+// one partition of it).  A block that waits longer than spin_cycles SM clocks
+// sets bit 4 of *err and returns false; every caller then leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks,
+                                             long long spin_cycles = kBarrierSpinCycles) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* vgen = bar + 1;
@@ -47,7 +48,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned n
             const long long t0 = clock64();
             while (*vgen == gen) {
                 __nanosleep(32);
-                if (clock64() - t0 > kBarrierSpinCycles) {
+                if (clock64() - t0 > spin_cycles) {
                     atomicOr(err, 4);
                     break;
                 }

@@ -244,6 +244,7 @@ struct CgCtl {
     double* relres_out;  // [R]
     long long* iter_acc; // nullable: iterations are added here (device counter)
     int* status_acc;     // nullable: bit 8 set when an RHS misses rtol
+    long long spin_cycles;   // grid-barrier wait limit (SM clocks)
 };
 
 // Per-block partial layout (stride 10 R): phase-1 partials double-buffered by
@@ -252,6 +253,23 @@ struct CgCtl {
 // phase-2 partials at [4R, 5R), init-1 partials at [6R, 9R).
 template <int R>
 constexpr int kCgStride = 10 * R;
+
+// Device error word of a solve (bit 1 breakdown, 4 barrier time-out, 16 stage-ring
+// time-out) folded into the caller's status accumulator, so that solves issued
+// without a host read-back (wave steps) still report it.
+__device__ __forceinline__ void cg_report(const CgCtl& c) {
+    if (threadIdx.x == 0 && c.status_acc) {
+        const int e = *((volatile int*)c.err);
+        if (e) atomicOr(c.status_acc, e);
+    }
+}
+
+
+}  // namespace iga
+
+#include "pcg_brick.cuh"
+
+namespace iga {
 
 template <int DIM, int P, typename T, int R>
 __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) pcg_persistent_kernel(CgVecs<T> v, CgCtl c) {
@@ -268,11 +286,11 @@ __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) 
     block_sum<3 * R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < 3 * R) c.partials[(size_t)blockIdx.x * S + 6 * R + threadIdx.x] = red[threadIdx.x];
     if (threadIdx.x < R) active[threadIdx.x] = 1;
-    if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
+    if (!grid_barrier(c.bar, c.err, gridDim.x, c.spin_cycles)) return cg_report(c);
     cg_phase2<DIM, P, T, R>(v, active, part, sdl);
     block_sum<R, kCgWarps>(part, wsum, red);
     if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
-    if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
+    if (!grid_barrier(c.bar, c.err, gridDim.x, c.spin_cycles)) return cg_report(c);
     grid_sum<3 * R>(c.partials, gridDim.x, S, 6 * R, red);
     grid_sum<R>(c.partials, gridDim.x, S, 4 * R, red2);
     if (threadIdx.x < R) {
@@ -304,11 +322,11 @@ __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) 
         cg_phase1<T, R>(v, alpha, beta, active, part);
         block_sum<2 * R, kCgWarps>(part, wsum, red);
         if (threadIdx.x < 2 * R) c.partials[(size_t)blockIdx.x * S + off1 + threadIdx.x] = red[threadIdx.x];
-        if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
+        if (!grid_barrier(c.bar, c.err, gridDim.x, c.spin_cycles)) return cg_report(c);
         cg_phase2<DIM, P, T, R>(v, active, part, sdl);
         block_sum<R, kCgWarps>(part, wsum, red);
         if (threadIdx.x < R) c.partials[(size_t)blockIdx.x * S + 4 * R + threadIdx.x] = red[threadIdx.x];
-        if (!grid_barrier(c.bar, c.err, gridDim.x)) return;
+        if (!grid_barrier(c.bar, c.err, gridDim.x, c.spin_cycles)) return cg_report(c);
         grid_sum<2 * R>(c.partials, gridDim.x, S, off1, red);
         grid_sum<R>(c.partials, gridDim.x, S, 4 * R, red2);
         if (threadIdx.x < R) {
@@ -334,6 +352,7 @@ __global__ void __launch_bounds__(kCgThreads, (R == 1 ? kCgMaxBlocksPerSM : 1)) 
         if (c.iter_acc) atomicAdd((unsigned long long*)c.iter_acc, (unsigned long long)iters[r]);
         if (c.status_acc && c.rtol > 0.0 && rel > c.rtol) atomicOr(c.status_acc, 8);
     }
+    if (blockIdx.x == 0) cg_report(c);
 }
 
 // ---------------------------------------------------------------- plain schedule kernels
@@ -560,8 +579,9 @@ __global__ void cgg_zero_kernel(CgVecs<T> v, const CgGState* gs) {
 
 template <int R>
 __global__ void cgg_finish_kernel(const CgGState* gs, double rtol, int* iters_out, double* relres_out,
-                                  long long* iter_acc, int* status_acc) {
+                                  long long* iter_acc, int* status_acc, const int* err) {
     const int r = threadIdx.x;
+    if (r == 0 && status_acc && *err) atomicOr(status_acc, *err);
     if (r >= R) return;
     const double rel = gs->bnorm[r] > 0.0 ? sqrt(gs->rr[r]) / gs->bnorm[r] : 0.0;
     iters_out[r] = gs->iters[r];
@@ -616,7 +636,7 @@ static int cgg_launch(CgVecs<T> v, double* partials, CgGState* gs, int* err, dou
             void* a_p2[] = {&v, &partials, &gs, &rtol, &max_it, &err, &loop};
             void* a_zero[] = {&v, &gs};
             void* a_p1[] = {&v, &partials, &gs};
-            void* a_fin[] = {&gs, &rtol, &iters_out, &relres_out, &iter_acc, &status_acc};
+            void* a_fin[] = {&gs, &rtol, &iters_out, &relres_out, &iter_acc, &status_acc, &err};
             bool ok = kernel_node(g, (const void*)cgg_init1_kernel<DIM, P, T, R>, a_init1, nullptr, 0, grid, kGThreads,
                                   &n_init1) &&
                       kernel_node(g, (const void*)cgg_phase2_kernel<DIM, P, T, R, true>, a_p2, &n_init1, 1, grid,
@@ -658,6 +678,55 @@ static int cg_blocks() {
         nb = std::max(1, sms * std::max(1, std::min(per, kCgMaxBlocksPerSM)));
     }
     return nb;
+}
+
+// Brick form of the persistent solve (FP32, one right-hand side, 3-D operators
+// whose brick form the mass apply uses).  Returns false when it does not apply
+// (the grid-stride persistent kernel runs instead); a failed launch is reported
+// through the CUDA error state like the other launches.
+template <int DIM, int P, typename T, int R>
+static bool brick_pcg_launch(const iga_ops* ops, CgVecs<T>& v, CgCtl& c, cudaStream_t st) {
+#ifdef IGA_BOUNDS_CHECK
+    (void)ops; (void)v; (void)c; (void)st;
+    return false;
+#else
+    if constexpr (DIM != 3 || sizeof(T) != 4 || R != 1 || P > 2) {
+        (void)ops; (void)v; (void)c; (void)st;
+        return false;
+    } else {
+        if (!brick_usable(ops, IGA_OP_M)) return false;
+        const BrickOps& bo = *ops->brick;
+        const size_t smem = kBrickPcgHeader + sizeof(float) * ((size_t)bo.ns * bo.stage_floats + bo.xt_floats);
+        if (smem > 227 * 1024) return false;
+        const int threads = (bo.ncw + 1) * 32;
+        auto fn3 = pcg_brick_kernel<P, 3>;
+        auto fn2 = pcg_brick_kernel<P, 2>;
+        const void* fn = bo.ns == 3 ? (const void*)fn3 : (const void*)fn2;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        int per = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1 ||
+            bo.nbricks > per * sms) {
+            cudaGetLastError();
+            return false;
+        }
+        const BrickMaps* maps = &bo.mapM;
+        const BrickDesc* bricks = bo.bricks.as<BrickDesc>();
+        int nF = ops->nM, sf = bo.stage_floats;
+        void* args[] = {(void*)maps, (void*)&bricks, &nF, &sf, &v, &c};
+        const cudaError_t e = cudaLaunchCooperativeKernel(fn, bo.nbricks, threads, args, smem, st);
+        count_launch();
+        if (e != cudaSuccess) {
+            cuda_fail(e, "cudaLaunchCooperativeKernel(pcg_brick)");
+            return false;
+        }
+        return true;
+    }
+#endif
 }
 
 template <int DIM, int P, typename T, int R>
@@ -708,6 +777,7 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
         c.relres_out = w.relres;
         c.iter_acc = iter_acc;
         c.status_acc = status_acc;
+        c.spin_cycles = kBarrierSpinCycles;
         bool use_graph = (flags & IGA_SOLVE_GRAPH) != 0;
         if (use_graph) {
             // a graph launch is not issued into a stream under capture: persistent schedule there
@@ -719,7 +789,7 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
             const int rc = cgg_launch<DIM, P, T, R>(v, w.partials, (CgGState*)w.gs, w.err, rtol, max_it, ggrid,
                                                    w.iters, w.relres, iter_acc, status_acc, st);
             if (rc) return rc;
-        } else {
+        } else if (!brick_pcg_launch<DIM, P, T, R>(ops, v, c, st)) {
             void* args[] = {&v, &c};
             cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_persistent_kernel<DIM, P, T, R>, nblocks,
                                                         kCgThreads, args, 0, st);
@@ -745,6 +815,7 @@ static int pcg_chunk(const iga_ops* ops, const T* b, T* x, long long ldu, double
             IGA_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
             IGA_CUDA(cudaStreamSynchronize(st));
             if (err & 4) return fail(IGA_ERR_TIMEOUT, "grid barrier timed out in pcg");
+            if (err & 16) return fail(IGA_ERR_TIMEOUT, "a stage of the brick field ring timed out in pcg");
             if (err & 1) return fail(IGA_ERR_NONFINITE, "CG breakdown: (p, M p) <= 0 or non-finite");
         }
     } else {
@@ -938,6 +1009,12 @@ extern "C" int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void
         int rc = mops->work.alloc(need);
         if (rc) return rc;
     }
-    return mass_solve_impl(ops, dtype, b, x, ops->N, nrhs, rtol, max_it, flags, iters_out, relres_out,
+    // the statistics are always read back (synchronising the stream), so that a
+    // missed tolerance, a breakdown or a time-out is returned also when the caller
+    // passes no statistics arrays
+    std::vector<int> it_local(iters_out ? 0 : nrhs);
+    std::vector<double> rr_local(relres_out ? 0 : nrhs);
+    return mass_solve_impl(ops, dtype, b, x, ops->N, nrhs, rtol, max_it, flags,
+                           iters_out ? iters_out : it_local.data(), relres_out ? relres_out : rr_local.data(),
                            (cudaStream_t)stream, mops->work.ptr, mops->work.bytes, nullptr, nullptr);
 }

@@ -309,6 +309,8 @@ static int wave_step_typed(iga_wave* w, int nsteps, cudaStream_t st) {
     }
     destroy_events();
     if (e != cudaSuccess) return cuda_fail(e, "wave_step");
+    if (st_h & (4 | 16)) return fail(IGA_ERR_TIMEOUT, "a bounded device wait timed out in a CG solve of wave_step");
+    if (st_h & 1) return fail(IGA_ERR_NONFINITE, "CG breakdown in a solve of wave_step");
     if (st_h & 8) return fail(IGA_ERR_NOT_CONVERGED, "a CG solve in wave_step missed its tolerance");
     return IGA_OK;
 }

@@ -116,3 +116,65 @@ def test_path_selection_errors():
     iga.iga_ops_set_path(ops, iga.IGA_PATH_ROWS)
     iga.iga_ops_destroy(ops)
     iga.iga_space_destroy(space)
+
+
+# ---------------------------------------------------------------- brick form of the mass solve
+def _solve(ops, path, b, x0, rtol, max_it, allow_nc=False):
+    iga.iga_ops_set_path(ops, path)
+    bg = torch.tensor(b[None], device="cuda")
+    xg = torch.tensor(x0[None], device="cuda")
+    rc, iters, rel = iga.iga_mass_solve(ops, iga.IGA_F32, bg, xg, 1, rtol, max_it, allow_not_converged=allow_nc)
+    iga.iga_ops_set_path(ops, iga.IGA_PATH_AUTO)
+    return rc, xg.cpu().numpy()[0].astype(np.float64), iters[0], rel[0]
+
+
+@pytest.mark.parametrize("name", ["cube12_p2", "cube20_p2_theta", "cube27_p2_odd", "cube14_p1"])
+def test_brick_pcg_iterates_match_oracle_pcg(name):
+    """Fixed 25 iterations (rtol = 0) of the brick-form persistent PCG against the FP64
+    oracle PCG on the same FP32-rounded operator and inputs (FP32 bar 2e-5 of the largest
+    iterate entry) and against the row-kernel persistent PCG (same recurrence and
+    precision; the FP32 mass apply sums in another order)."""
+    from oracle.wave import pcg
+    sp, _, M = oracle_ops(name)
+    _, ops = gpu_ops(name)
+    M = M.copy()
+    dinv = (1.0 / M.diagonal()).astype(np.float32).astype(np.float64)
+    M.data = M.data.astype(np.float32).astype(np.float64)
+    b = inputs.vectors(sp.N, 1)[0].astype(np.float32)
+    x0 = (0.1 * inputs.vectors(sp.N, 1, seed=99)[0]).astype(np.float32)
+    xr, it, _ = pcg(M, b.astype(np.float64), x0.astype(np.float64), dinv, 0.0, 25)
+    rc, xb, ib, _ = _solve(ops, iga.IGA_PATH_BRICK, b, x0, 0.0, 25)
+    _, xw, iw, _ = _solve(ops, iga.IGA_PATH_ROWS, b, x0, 0.0, 25)
+    assert ib == 25 and iw == 25 and it == 25
+    scale = np.abs(xr).max()
+    assert np.abs(xb - xr).max() <= 2e-5 * scale
+    assert np.abs(xb - xw).max() <= 2e-5 * scale
+
+
+def test_brick_pcg_converges_like_rows_and_is_deterministic():
+    sp, _, M = oracle_ops("cube27_p2_odd")
+    _, ops = gpu_ops("cube27_p2_odd")
+    b = inputs.vectors(sp.N, 1)[0].astype(np.float32)
+    x0 = np.zeros(sp.N, dtype=np.float32)
+    _, xb, ib, rb = _solve(ops, iga.IGA_PATH_BRICK, b, x0, 1e-6, 500)
+    _, xb2, ib2, _ = _solve(ops, iga.IGA_PATH_BRICK, b, x0, 1e-6, 500)
+    _, xw, iw, rw = _solve(ops, iga.IGA_PATH_ROWS, b, x0, 1e-6, 500)
+    assert rb <= 1e-6 and rw <= 1e-6 and abs(ib - iw) <= 1
+    assert ib == ib2 and np.array_equal(xb, xb2)
+    # true residual of the FP32-stored solution: its rounding alone leaves about
+    # 6e-8 |M| |x|, here ~6e-6 ||b|| (the recursive FP64 residual is the one below 1e-6)
+    r = b.astype(np.float64) - M @ xb
+    assert np.linalg.norm(r) <= 2e-5 * np.linalg.norm(b)
+    assert np.abs(xb - xw).max() <= 1e-4 * np.abs(xw).max()
+
+
+def test_brick_pcg_zero_rhs_and_non_convergence():
+    sp, _, _ = oracle_ops("cube20_p2_theta")
+    _, ops = gpu_ops("cube20_p2_theta")
+    b = np.zeros(sp.N, dtype=np.float32)
+    _, x, it, _ = _solve(ops, iga.IGA_PATH_BRICK, b, np.ones(sp.N, dtype=np.float32), 1e-6, 50)
+    assert it == 0 and np.all(x == 0.0)
+    b = inputs.vectors(sp.N, 1)[0].astype(np.float32)
+    rc, _, it, rel = _solve(ops, iga.IGA_PATH_BRICK, b, np.zeros(sp.N, dtype=np.float32), 1e-9, 2,
+                            allow_nc=True)
+    assert rc == iga.IGA_ERR_NOT_CONVERGED and it == 2 and rel > 1e-9
