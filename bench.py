@@ -43,17 +43,24 @@ def load_peaks():
         return None
 
 
-PCG_PROFILE = os.path.join(ROOT, "profiles", "stencil_apply_and_pcg_cube80_p2.md")
-PCG_SOURCES = ["solve.cu", "cg.cuh", "stencil.cuh"]
+# ncu summaries of the two persistent PCG kernels, with the sources hashed when the
+# counters were taken
+PCG_PROFILES = {
+    "pcg_persistent_kernel": (os.path.join(ROOT, "profiles", "stencil_apply_and_pcg_cube80_p2.md"),
+                              ["solve.cu", "cg.cuh", "stencil.cuh"]),
+    "pcg_brick_kernel": (os.path.join(ROOT, "profiles", "pcg_brick_kernel_cube80_p2.md"),
+                         ["solve.cu", "cg.cuh", "pcg_brick.cuh", "brick.cuh"]),
+}
 
 
-def pcg_profiled_traffic():
-    """DRAM bytes per row (per solve, per iteration) of the persistent PCG from the
+def pcg_profiled_traffic(kernel):
+    """DRAM bytes per row (per solve, per iteration) of a persistent PCG kernel from its
     committed ncu summary, or None when the kernel sources changed since the capture."""
     import hashlib
     try:
+        path, sources = PCG_PROFILES[kernel]
         vals = {}
-        with open(PCG_PROFILE) as f:
+        with open(path) as f:
             for line in f:
                 line = line.strip()
                 for key in ("pcg_dram_bytes_per_row_init", "pcg_dram_bytes_per_row_iteration",
@@ -61,7 +68,7 @@ def pcg_profiled_traffic():
                     if line.startswith(key + ":"):
                         vals[key] = line.split(":", 1)[1].strip()
         h = hashlib.sha256()
-        for name in PCG_SOURCES:
+        for name in sources:
             with open(os.path.join(ROOT, "paper_2004_05197_gb300", "csrc", name), "rb") as f:
                 h.update(f.read())
         if h.hexdigest()[:16] != vals.get("kernel_sources_sha256_16"):
@@ -240,12 +247,19 @@ def run_ours(args, rank, world, device):
     # one shot: every launch is one solve and the device counter holds its iterations
     cg_bytes_total = (cg_solves * init_b + cg_it * it_b) * N if args.nshot == 1 else None
     achieved = cg_bytes_total / (cg_ms / 1e3) / 1e9 if cg_bytes_total else None
+    # which persistent kernel ran: the brick form for an FP32 single-RHS solve on an
+    # operator whose M~ apply runs on bricks
+    brick_paths = iga.iga_ops_brick_info(ops, with_paths=True)[4]
+    if args.solve == "graph":
+        kernel = "pcg graph (cgg_phase1_kernel + cgg_phase2_kernel)"
+    else:
+        kernel = "pcg_brick_kernel" if (args.nshot == 1 and brick_paths & 2) else "pcg_persistent_kernel"
     # ncu DRAM bytes of the same kernel on the n_el = 80 case, scaled to this launch by rows
     # and by the mean iterations per launch (traffic grows in proportion to both)
-    prof = pcg_profiled_traffic() if (args.nshot == 1 and args.solve == "persistent") else None
+    prof = pcg_profiled_traffic(kernel) if (args.nshot == 1 and kernel in PCG_PROFILES) else None
     traffic = ((prof[0] + prof[1] * cg_it / max(1, cg_solves)) * N) if prof else None
     traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, %s, scaled by rows and "
-                   "iterations per launch" % os.path.relpath(PCG_PROFILE, ROOT)) if prof else None
+                   "iterations per launch" % os.path.relpath(PCG_PROFILES[kernel][0], ROOT)) if prof else None
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs") if peaks else None
     peak_src = "measured" if peak else "fallback"
@@ -268,8 +282,7 @@ def run_ours(args, rank, world, device):
         "config": workload_config(args, world),
         "components": comps,
         "roofline": {"bound": "hbm",
-                     "kernel": ("pcg graph (cgg_phase1_kernel + cgg_phase2_kernel)" if args.solve == "graph"
-                                else "pcg_persistent_kernel"),
+                     "kernel": kernel,
                      "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -409,44 +422,97 @@ def next_rows_leg(ctx, args):
     return {"next_rows": out}
 
 
-def fp64_plain_and_error(ctx, args):
-    """FP64 plain single-shot schedule on the same workload (bounded steps) and the FP32 error."""
+def fp64_forms_and_error(ctx, args):
+    """Single-shot FP64 forms of the bench workload beside the FP32 persistent form.
+
+    * FP64 with the plain CG schedule (a host round trip per CG iteration), with the
+      graph schedule (phase launches in a CUDA graph, convergence on the device) and with
+      the persistent schedule: shot-steps/s, the first two on `compare_steps` steps, the
+      persistent one on all steps of the workload;
+    * FP32 error: relative L2 distance of the FP32 state after all steps (the final state
+      of the timed FP32 pass) from the FP64 persistent state after the same steps (CG
+      rtol 1e-10).  The FP64 waves are pinned to the oracle by the wave parity tests.
+    """
     import numpy as np
     import torch
 
     from paper_2004_05197_gb300 import iga
     space, ops, wave, w, nsteps, dt, src, rec = ctx
-    P = min(args.compare_steps, nsteps)
     N = iga.iga_ops_info_get(ops).N
     res = {}
-    w64 = iga.iga_wave_create(ops, 1, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1,
-                              cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN,
-                              cg_guess=args.cg_guess)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    iga.iga_wave_step(w64, P)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t
-    res["fp64_plain_shot_steps_per_s"] = P / t
-    res["fp64_plain_steps"] = P
-    u64 = torch.empty((1, N), dtype=torch.float64, device="cuda")
-    iga.iga_wave_get_state(w64, u64)
-    w32 = iga.iga_wave_create(ops, 1, iga.IGA_F32, dt, src_pos=src, f0=10.0, t0=0.1,
-                              cg_rtol=args.cg_rtol, cg_max_it=args.cg_max_it, cg_guess=args.cg_guess)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    iga.iga_wave_step(w32, P)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t
-    res["fp32_single_shot_steps_per_s"] = P / t
+    u64 = None
+    for name, flags, P in (("plain", iga.IGA_SOLVE_PLAIN, min(args.compare_steps, nsteps)),
+                           ("graph", iga.IGA_SOLVE_GRAPH, min(args.compare_steps, nsteps)),
+                           ("persistent", 0, nsteps)):
+        w64 = iga.iga_wave_create(ops, 1, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1, cg_rtol=1e-10,
+                                  cg_max_it=args.cg_max_it, solve_flags=flags, cg_guess=args.cg_guess)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        iga.iga_wave_step(w64, P)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t
+        res["fp64_%s_shot_steps_per_s" % name] = P / t
+        res["fp64_%s_steps" % name] = P
+        if name == "persistent":
+            u64 = torch.empty((1, N), dtype=torch.float64, device="cuda")
+            iga.iga_wave_get_state(w64, u64)
+        iga.iga_wave_destroy(w64)
     u32 = torch.empty((1, N), dtype=torch.float32, device="cuda")
-    iga.iga_wave_get_state(w32, u32)
+    iga.iga_wave_get_state(wave, u32)
     torch.cuda.synchronize()
     a = u32.double().cpu().numpy()
     b = u64.cpu().numpy()
     res["fp32_vs_fp64_rel_l2_error"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    iga.iga_wave_destroy(w64)
-    iga.iga_wave_destroy(w32)
+    res["fp32_vs_fp64_steps"] = nsteps
+    fastest = max(res["fp64_plain_shot_steps_per_s"], res["fp64_graph_shot_steps_per_s"],
+                  res["fp64_persistent_shot_steps_per_s"])
+    res["fp64_fastest_single_shot_shot_steps_per_s"] = fastest
+    return res
+
+
+def config2_leg(args):
+    """2-D p=3 annulus, 512^2 elements, c = 1 + 0.5 sin(2 pi x) cos(2 pi y), q = 3, M = 8,
+    Ricker f0 = 10 at s = (0.5, 0.5), dt = 0.1 h, `config2_steps` steps: FP32 persistent
+    (CG rtol as the bench) against FP64 persistent (CG rtol 1e-10), shot-steps/s of both
+    (assembly not included) and the FP32 relative L2 error after all steps.  Its FP32
+    operators (52 MB) are L2-resident, so its rates are L2-bound, not HBM-bound."""
+    import numpy as np
+    import torch
+
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300 import workloads as W
+    w = W.scaled("annulus512_p3")
+    P = args.config2_steps
+    sp = W.make_space(w)
+    ops = iga.iga_surrogate_assemble(sp, w["p"], w["q"], w["M"])
+    N = iga.iga_ops_info_get(ops).N
+    src = W.source_position(w)[None]
+    res = {"config2_workload": "annulus512_p3, %d steps" % P}
+    states = {}
+    for name, dtype, rtol in (("fp32", iga.IGA_F32, args.cg_rtol), ("fp64", iga.IGA_F64, 1e-10)):
+        wv = iga.iga_wave_create(ops, 1, dtype, W.dt_of(w), src_pos=src, f0=10.0, t0=0.1, cg_rtol=rtol,
+                                 cg_max_it=args.cg_max_it, cg_guess=args.cg_guess)
+        iga.iga_wave_step(wv, 5)                     # warm-up, then restart
+        iga.iga_wave_reset(wv, ops)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        iga.iga_wave_step(wv, P)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t
+        res["config2_%s_shot_steps_per_s" % name] = P / t
+        st = iga.iga_wave_stats_get(wv)
+        res["config2_%s_cg_iterations_per_step" % name] = st.cg_iterations / max(1, st.steps)
+        u = torch.empty((1, N), dtype=torch.float64 if dtype == iga.IGA_F64 else torch.float32, device="cuda")
+        iga.iga_wave_get_state(wv, u)
+        torch.cuda.synchronize()
+        states[name] = u.double().cpu().numpy()
+        iga.iga_wave_destroy(wv)
+    a, b = states["fp32"], states["fp64"]
+    res["config2_fp32_vs_fp64_rel_l2_error"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    res["config2_fp32_over_fp64"] = res["config2_fp32_shot_steps_per_s"] / res["config2_fp64_shot_steps_per_s"]
+    res["config2_l2_resident"] = "FP32 fields 52 MB, FP64 fields 106 MB: both below the 129 MB L2"
+    iga.iga_ops_destroy(ops)
+    iga.iga_space_destroy(sp)
     return res
 
 
@@ -498,10 +564,10 @@ def run_batched(args):
     (c = 1 + 0.5 sin(2 pi x) cos(2 pi y), q = 3, M = 8, dt = 0.1 h), 16 Ricker shots
     each at seeded uniform positions in [0.1, 0.9]^2: 64 shots advanced together
     in one persistent cooperative launch replayed from a CUDA graph (16 shots per
-    mesh as two right-hand-side groups of 8).  The plain form runs one shot at a
-    time in FP64 with the non-persistent CG schedule; its rate is measured on a
-    few steps per mesh and the error of the FP32 batch against FP64 is taken on
-    the same window.
+    mesh as two right-hand-side groups of 8).  Against it, one shot at a time in
+    FP64 with the plain (host round trip per CG iteration), graph and persistent
+    CG schedules, and the error of the FP32 batch against the FP64 persistent
+    shot after all steps.
     """
     import numpy as np
     import torch
@@ -549,40 +615,46 @@ def run_batched(args):
     iga.iga_batch_destroy(b)
     for wv in waves:
         iga.iga_wave_destroy(wv)
-    # plain FP64 single-shot schedule (first shot of each mesh) timed on `plain_steps`
-    # steps; the FP64 reference for the error is the same shot run for all steps with
-    # the persistent FP64 solver (same arithmetic, CG rtol 1e-10)
-    plain_t, plain_ss, errs = 0.0, 0, []
+    # FP64 single-shot forms (first shot of each mesh): the plain schedule and the graph
+    # schedule timed on `plain_steps` steps, the persistent schedule on all steps; the
+    # persistent FP64 wave (CG rtol 1e-10) is also the reference of the FP32 error
+    t_form = {"plain": 0.0, "graph": 0.0, "persistent": 0.0}
+    ss_form = {"plain": 0, "graph": 0, "persistent": 0}
+    errs = []
     for k, (w, sp, ops, src) in enumerate(meshes):
-        wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
-                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=iga.IGA_SOLVE_PLAIN,
-                                 cfl_check=0, cg_guess=args.batched_cg_guess)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        iga.iga_wave_step(wv, args.plain_steps)
-        torch.cuda.synchronize()
-        plain_t += time.perf_counter() - t
-        plain_ss += args.plain_steps
-        iga.iga_wave_destroy(wv)
-        wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
-                                 cg_rtol=1e-10, cg_max_it=args.cg_max_it, cfl_check=0, cg_guess=args.batched_cg_guess)
-        iga.iga_wave_step(wv, nsteps)
-        N = iga.iga_ops_info_get(ops).N
-        u = torch.empty((1, N), dtype=torch.float64, device="cuda")
-        iga.iga_wave_get_state(wv, u)
-        torch.cuda.synchronize()
-        ref = u[0].cpu().numpy()
-        errs.append(float(np.linalg.norm(u32[k] - ref) / max(np.linalg.norm(ref), 1e-300)))
-        iga.iga_wave_destroy(wv)
+        for name, flags, P in (("plain", iga.IGA_SOLVE_PLAIN, args.plain_steps),
+                               ("graph", iga.IGA_SOLVE_GRAPH, args.plain_steps), ("persistent", 0, nsteps)):
+            wv = iga.iga_wave_create(ops, 1, iga.IGA_F64, W.dt_of(w), src_pos=src[:1], f0=10.0, t0=0.1,
+                                     cg_rtol=1e-10, cg_max_it=args.cg_max_it, solve_flags=flags,
+                                     cfl_check=0, cg_guess=args.batched_cg_guess)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            iga.iga_wave_step(wv, P)
+            torch.cuda.synchronize()
+            t_form[name] += time.perf_counter() - t
+            ss_form[name] += P
+            if name == "persistent":
+                N = iga.iga_ops_info_get(ops).N
+                u = torch.empty((1, N), dtype=torch.float64, device="cuda")
+                iga.iga_wave_get_state(wv, u)
+                torch.cuda.synchronize()
+                ref = u[0].cpu().numpy()
+                errs.append(float(np.linalg.norm(u32[k] - ref) / max(np.linalg.norm(ref), 1e-300)))
+            iga.iga_wave_destroy(wv)
     for (w, sp, ops, src) in meshes:
         iga.iga_ops_destroy(ops)
         iga.iga_space_destroy(sp)
-    # a plain shot-step costs the same whichever shot it is: the mean over the four meshes
-    plain = plain_ss / plain_t
+    # a single-shot step costs the same whichever shot it is: rates over the four meshes
+    rate = {k: ss_form[k] / t_form[k] for k in t_form}
+    plain = rate["plain"]
+    fastest = max(rate.values())
     return {"batched_workload": "annulus p=3 meshes 128^2,256^2,384^2,512^2 x 16 Ricker shots, %d steps" % nsteps,
             "batched_fp32_shot_steps_per_s": batched, "batched_ms": ms,
             "plain_fp64_single_shot_shot_steps_per_s": plain,
+            "graph_fp64_single_shot_shot_steps_per_s": rate["graph"],
+            "persistent_fp64_single_shot_shot_steps_per_s": rate["persistent"],
             "batched_over_plain": batched / plain,
+            "batched_over_fastest_fp64_single_shot": batched / fastest,
             "batched_fp32_vs_fp64_rel_l2_error_max": max(errs),
             "batched_partition_blocks": part,
             "batched_cg_start": ("previous acceleration" if args.batched_cg_guess == 0 else
@@ -792,12 +864,15 @@ def main():
                     help="CG start of each step: polynomial extrapolation in time of this order (0: a^{n-1})")
     ap.add_argument("--solve", default="persistent", choices=["persistent", "graph"],
                     help="CG schedule of the FP32 waves")
-    ap.add_argument("--compare-steps", type=int, default=50)
+    ap.add_argument("--compare-steps", type=int, default=50,
+                    help="steps of the FP64 plain and graph single-shot rates (the persistent FP64 wave runs all steps)")
+    ap.add_argument("--config2-steps", type=int, default=2000,
+                    help="steps of the 2-D p=3 annulus 512^2 leg (0: skip it)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--oracle-rows", type=int, default=96)
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison leg")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-mesh leg")
     ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--batched-rtol", type=float, default=3e-7,
@@ -833,7 +908,9 @@ def main():
         if args.next_rows:
             out["components"].update(next_rows_leg(ctx, args))
         if not args.no_compare:
-            out["components"].update(fp64_plain_and_error(ctx, args))
+            out["components"].update(fp64_forms_and_error(ctx, args))
+        if args.config2_steps > 0:
+            out["components"].update(config2_leg(args))
         if args.e2e_steps > 0:
             out["e2e"] = run_e2e(args, ctx)
         if not args.no_batched:

@@ -216,8 +216,11 @@ int iga_stencil_apply(const iga_ops* ops, int which, int dtype, const void* x, v
 int iga_ops_set_path(iga_ops* ops, int path);
 /* Brick plan of an ops (all outputs nullable host pointers; zeros without a
  * brick form): bricks (= CTAs of a brick launch), threads per CTA, ring
- * stages, dynamic shared memory bytes per CTA.  Host-only. */
-int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stages, int* smem_bytes);
+ * stages, dynamic shared memory bytes per CTA, and brick_paths: which FP32
+ * operators run on brick kernels under the current path setting (bit 0: K~
+ * apply; bit 1: M~ apply and the persistent single-RHS mass solve).  Host-only. */
+int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stages, int* smem_bytes,
+                       int* brick_paths);
 
 /* mass_solve: Jacobi-PCG on M~ a = b for nrhs right-hand sides (device
  * pointers [nrhs][N] of `dtype`; x holds the initial guess on entry and the

@@ -412,12 +412,15 @@ extern "C" int iga_ops_set_path(iga_ops* ops, int path) {
     return IGA_OK;
 }
 
-extern "C" int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stages, int* smem_bytes) {
+extern "C" int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stages, int* smem_bytes,
+                                  int* brick_paths) {
     if (!ops) return fail(IGA_ERR_ARG, "null argument");
     const BrickOps* bo = ops->brick.get();
     if (nbricks) *nbricks = bo ? bo->nbricks : 0;
     if (threads) *threads = bo ? (bo->ncw + 1) * 32 : 0;
     if (stages) *stages = bo ? bo->ns : 0;
     if (smem_bytes) *smem_bytes = bo ? (int)bo->smem : 0;
+    if (brick_paths)
+        *brick_paths = (brick_usable(ops, IGA_OP_K) ? 1 : 0) | (brick_usable(ops, IGA_OP_M) ? 2 : 0);
     return IGA_OK;
 }

@@ -106,7 +106,7 @@ _sig = {
     "iga_ops_sample_indices": [_vp, C.POINTER(_i)],
     "iga_stencil_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
     "iga_ops_set_path": [_vp, _i],
-    "iga_ops_brick_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
+    "iga_ops_brick_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "iga_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_multipatch_create": [_i, C.POINTER(_vp), _i, C.POINTER(iga_interface), C.POINTER(_vp)],
     "iga_multipatch_destroy": [_vp],
@@ -249,11 +249,13 @@ def iga_ops_set_path(ops, path):
     _check(_lib.iga_ops_set_path(ops, path))
 
 
-def iga_ops_brick_info(ops):
-    """(bricks, threads per CTA, ring stages, shared-memory bytes per CTA); zeros without a brick form."""
-    v = [C.c_int() for _ in range(4)]
+def iga_ops_brick_info(ops, with_paths=False):
+    """(bricks, threads per CTA, ring stages, shared-memory bytes per CTA[, brick_paths]);
+    zeros without a brick form.  brick_paths: bit 0 K~ apply, bit 1 M~ apply and mass solve."""
+    v = [C.c_int() for _ in range(5)]
     _check(_lib.iga_ops_brick_info(ops, *[C.byref(t) for t in v]))
-    return tuple(t.value for t in v)
+    out = tuple(t.value for t in v)
+    return out if with_paths else out[:4]
 
 
 def iga_mass_solve(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_stats=True, stream=None,
