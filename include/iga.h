@@ -174,6 +174,8 @@ typedef struct iga_ops_info {
     int n_band_elements;    /* elements quadrated for the true entries */
     int n_sample_rows;      /* ns^dim */
     double t_sample_ms, t_band_ms, t_interp_ms, t_eval_ms, t_total_ms; /* device time */
+    long long workspace_bytes; /* CG workspace the library holds for iga_mass_solve on this
+                                  ops (0 until the first such call) */
 } iga_ops_info;
 int iga_ops_info_get(const iga_ops* ops, iga_ops_info* out);
 
@@ -189,9 +191,18 @@ int iga_ops_copy_samples(const iga_ops* ops, int which, double* dst, void* strea
 int iga_ops_sample_indices(const iga_ops* ops, int* host_dst);
 
 /* ---- matrix-free operators -----------------------------------------------
- * stencil_apply: y = A x for A = K~ (difference form) or M~, nrhs vectors,
- * x, y device pointers [nrhs][N] of `dtype` (float or double), y must not
- * alias x.  Each field element is read once per call for all nrhs vectors.
+ * stencil_apply: y = A x for A = K~ or M~, the surrogate matrices of
+ * Eq. DefinitionOfSurrogateMatrixSymmetric (mass) and
+ * Eq. DefinitionOfSurrogateMatrixSymmetricKernel (stiffness: off-diagonal
+ * entries from the stencil functions, diagonal = minus the off-diagonal row
+ * sum), applied matrix-free from the stored stencil data as Sec. 3.3 describes
+ * for matrix-free methods.  Row i reads its upper entries F_u[i] and, by
+ * symmetry, its lower entries F_u[i - Delta_u]; K~ is applied in the
+ * difference form (K~x)_i = sum_{j != i} K~_ij (x_j - x_i), exact on constants.
+ * nrhs vectors; x, y device pointers [nrhs][N] of `dtype` (float or double);
+ * y must not alias x (IGA_ERR_ARG).  Each field element is read once per call
+ * for all nrhs vectors (row kernels) or once per vector (brick kernels of 3-D
+ * FP32 operators, see iga_ops_set_path).  Asynchronous on `stream`.
  */
 int iga_stencil_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y,
                       int nrhs, void* stream);
@@ -222,9 +233,12 @@ int iga_ops_set_path(iga_ops* ops, int path);
 int iga_ops_brick_info(const iga_ops* ops, int* nbricks, int* threads, int* stages, int* smem_bytes,
                        int* brick_paths);
 
-/* mass_solve: Jacobi-PCG on M~ a = b for nrhs right-hand sides (device
+/* mass_solve: Jacobi-PCG on M~ a = b for nrhs right-hand sides.  The paper
+ * gives no solver for the consistent mass: the preconditioned CG here (Jacobi
+ * preconditioner, Chronopoulos-Gear arrangement of the recurrence, same iterates
+ * as textbook PCG) is the library's choice.  Arguments: device
  * pointers [nrhs][N] of `dtype`; x holds the initial guess on entry and the
- * solution on exit).  Stops each RHS when ||r||_2 <= rtol ||b||_2 (rtol = 0:
+ * solution on exit.  Stops each RHS when ||r||_2 <= rtol ||b||_2 (rtol = 0:
  * exactly max_it iterations).  FP32 dtype: FP32 fields / vectors, FP64
  * residual and dot products.  Default schedule: one persistent cooperative
  * launch for all iterations with device-side convergence; IGA_SOLVE_PLAIN:
@@ -270,6 +284,16 @@ int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nr
 int iga_mass_solve_noalloc(const iga_ops* ops, int dtype, const void* b, void* x, int nrhs,
                            double rtol, int max_it, unsigned flags, int* iters_out,
                            double* relres_out, void* stream);
+
+/* Self-test of the bounded grid barrier that the persistent CG kernels use (a
+ * failure-detection check that faults nothing): one cooperative launch of
+ * `blocks` blocks (1 <= blocks <= the SM count) whose barrier waits for
+ * `expected` arrivals, each waiting block giving up after limit_ms
+ * milliseconds of SM clock.  Returns IGA_OK when the barrier opened
+ * (expected <= blocks), IGA_ERR_TIMEOUT when the wait ran out (expected >
+ * blocks: the arrival that nothing makes); the device context stays usable
+ * either way.  Synchronises the stream. */
+int iga_barrier_selftest(int blocks, int expected, double limit_ms, void* stream);
 
 /* ---- spectrum --------------------------------------------------------------
  * Extreme eigenvalues of the pencil K~ v = lambda M~ v by k Lanczos steps in the
@@ -322,9 +346,13 @@ typedef struct iga_wave_desc {
 
 int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);
 int iga_wave_destroy(iga_wave* wave);
-/* Advances every shot by nsteps. Async on stream; returns IGA_ERR_NOT_CONVERGED
- * (after synchronising) if a CG solve missed its tolerance, IGA_ERR_ARG if the
- * trace buffer would overflow. */
+/* Advances every shot by nsteps of the leapfrog scheme M~ a^n = f^n - K~ u^n,
+ * u^{n+1} = 2 u^n - u^{n-1} + dt^2 a^n (the paper solves no transient problem
+ * with the surrogate matrices; Sec. 4.6 gives the setting, the scheme is this
+ * library's).  Async on stream; returns (after synchronising)
+ * IGA_ERR_NOT_CONVERGED if a CG solve missed its tolerance, IGA_ERR_NONFINITE
+ * on a CG breakdown, IGA_ERR_TIMEOUT if a bounded device wait of a solve gave
+ * up, IGA_ERR_ARG if the trace buffer would overflow. */
 int iga_wave_step(iga_wave* wave, int nsteps, void* stream);
 /* Copies u^n (and u^{n-1} if u_prev != NULL) into device buffers [nshot][N] of the
  * wave's dtype. Async. */

@@ -802,6 +802,7 @@ extern "C" int iga_ops_info_get(const iga_ops* ops, iga_ops_info* out) {
     out->t_interp_ms = ops->t_interp;
     out->t_eval_ms = ops->t_eval;
     out->t_total_ms = ops->t_total;
+    out->workspace_bytes = (long long)ops->work.bytes;
     return IGA_OK;
 }
 

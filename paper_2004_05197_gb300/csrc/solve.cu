@@ -1018,3 +1018,39 @@ extern "C" int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void
                            iters_out ? iters_out : it_local.data(), relres_out ? relres_out : rr_local.data(),
                            (cudaStream_t)stream, mops->work.ptr, mops->work.bytes, nullptr, nullptr);
 }
+
+// ---------------------------------------------------------------- barrier self-test
+namespace iga {
+__device__ unsigned g_selftest_bar[2];
+__device__ int g_selftest_err;
+__global__ void barrier_selftest_kernel(unsigned expected, long long spin_cycles) {
+    grid_barrier(g_selftest_bar, &g_selftest_err, expected, spin_cycles);
+}
+}  // namespace iga
+
+extern "C" int iga_barrier_selftest(int blocks, int expected, double limit_ms, void* stream) {
+    int dev = 0, sms = 0, khz = 0;
+    IGA_CUDA(cudaGetDevice(&dev));
+    IGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    IGA_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    if (blocks < 1 || blocks > sms || expected < 1 || !(limit_ms > 0.0) || limit_ms > 10000.0)
+        return fail(IGA_ERR_ARG, "need 1 <= blocks <= SMs, expected >= 1, 0 < limit_ms <= 10000");
+    cudaStream_t st = (cudaStream_t)stream;
+    void* bar = nullptr;
+    void* err = nullptr;
+    IGA_CUDA(cudaGetSymbolAddress(&bar, g_selftest_bar));
+    IGA_CUDA(cudaGetSymbolAddress(&err, g_selftest_err));
+    IGA_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+    IGA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    // the limit in SM clocks at the maximum clock: at a lower clock the wait is longer
+    unsigned ex = (unsigned)expected;
+    long long spin = (long long)(limit_ms * (double)khz);
+    void* args[] = {&ex, &spin};
+    IGA_CUDA(cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, blocks, 32, args, 0, st));
+    count_launch();
+    int e = 0;
+    IGA_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+    if (e & 4) return fail(IGA_ERR_TIMEOUT, "grid barrier self-test: the wait ran out");
+    return IGA_OK;
+}

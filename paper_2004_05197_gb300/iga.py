@@ -42,6 +42,7 @@ EXPORTED = [
     "iga_mass_solve_noalloc", "iga_sampling_length_for_mesh",
     "iga_multipatch_create", "iga_multipatch_destroy", "iga_multipatch_size", "iga_multipatch_global_index",
     "iga_multipatch_apply", "iga_multipatch_mass_solve", "iga_ops_set_path", "iga_ops_brick_info",
+    "iga_barrier_selftest",
 ]
 
 
@@ -69,7 +70,8 @@ class iga_ops_info(C.Structure):
                 ("p", C.c_int), ("q", C.c_int), ("M", C.c_int), ("nK", C.c_int), ("nM", C.c_int),
                 ("D", C.c_int), ("ns", C.c_int), ("n_band_elements", C.c_int),
                 ("n_sample_rows", C.c_int), ("t_sample_ms", C.c_double), ("t_band_ms", C.c_double),
-                ("t_interp_ms", C.c_double), ("t_eval_ms", C.c_double), ("t_total_ms", C.c_double)]
+                ("t_interp_ms", C.c_double), ("t_eval_ms", C.c_double), ("t_total_ms", C.c_double),
+                ("workspace_bytes", C.c_longlong)]
 
 
 class iga_interface(C.Structure):
@@ -106,6 +108,7 @@ _sig = {
     "iga_ops_sample_indices": [_vp, C.POINTER(_i)],
     "iga_stencil_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
     "iga_ops_set_path": [_vp, _i],
+    "iga_barrier_selftest": [_i, _i, _d, _vp],
     "iga_ops_brick_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "iga_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_multipatch_create": [_i, C.POINTER(_vp), _i, C.POINTER(iga_interface), C.POINTER(_vp)],
@@ -256,6 +259,12 @@ def iga_ops_brick_info(ops, with_paths=False):
     _check(_lib.iga_ops_brick_info(ops, *[C.byref(t) for t in v]))
     out = tuple(t.value for t in v)
     return out if with_paths else out[:4]
+
+
+def iga_barrier_selftest(blocks, expected, limit_ms, stream=None):
+    """Status code of the bounded grid-barrier self-test (IGA_OK or IGA_ERR_TIMEOUT)."""
+    return _check(_lib.iga_barrier_selftest(blocks, expected, limit_ms, _stream(stream)),
+                  (IGA_OK, IGA_ERR_TIMEOUT))
 
 
 def iga_mass_solve(ops, dtype, b, x, nrhs, rtol, max_it, flags=0, want_stats=True, stream=None,

@@ -90,6 +90,21 @@ def test_fields_fp64_match_oracle(name):
     assert np.abs(gM - oM).max() <= 1e-12 * np.abs(oM).max()
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_fields_match_oracle_per_entry(name):
+    """Every stored entry on its own scale: |gpu - oracle| <= 1e-12 |oracle| + 1e-14 max|oracle|
+    (the floor covers entries that cancel to nearly zero, whose rounding is set by the
+    size of the terms that cancel)."""
+    sp, S, SK, SM, _, _ = oracle_full(name)
+    _, ops = gpu_ops(name)
+    oK, oM = oracle_fields(sp, SK, SM)
+    for g, o in ((fields(ops, iga.IGA_OP_K, iga.IGA_F64), oK), (fields(ops, iga.IGA_OP_M, iga.IGA_F64), oM)):
+        bound = 1e-12 * np.abs(o) + 1e-14 * np.abs(o).max()
+        ratio = (np.abs(g - o) / bound).max()
+        print(name, "worst per-entry error / bound", ratio)
+        assert ratio <= 1.0
+
+
 @pytest.mark.parametrize("name", ["annulus64_p2", "cube20_p2_theta"])
 def test_fields_fp32_are_rounded_fp64(name):
     _, ops = gpu_ops(name)
@@ -398,6 +413,8 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     # cond(M~) * 2^-24 ~ 1e-5 whatever the CG tolerance
     tol = 2e-5 if f32 else 1e-11
     assert err <= tol and terr <= tol
+    # the state in the max norm as well: no single coefficient off by more than tol
+    assert np.abs(ug - ur).max() <= tol * np.abs(ur).max()
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

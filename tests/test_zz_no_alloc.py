@@ -4,8 +4,11 @@ iga_mass_solve (library-allocated workspace) on the same seeded inputs.
 Both entry points run the same solver, so the tolerance is the one the other
 GPU tests use for the CG paths: 1e-12 relative for FP64, 2e-5 for FP32.  Each
 case calls the no-alloc entry twice in a row, so the second call runs on
-scratch the first one left behind.  The file sorts last so that the suite also
-exercises the entry point after every other test has used the device.
+scratch the first one left behind.  On an ops that never ran iga_mass_solve,
+the no-alloc calls leave the library's CG workspace at zero bytes and, after a
+first call, do not change the device's free memory.  The file sorts last so that
+the suite also exercises the entry point after every other test has used the
+device.
 """
 import numpy as np
 import pytest
@@ -82,6 +85,66 @@ def test_noalloc_rejects_workspace_beyond_the_fixed_array():
         torch.cuda.synchronize()
         err = (x1 - x1_ref).abs().max().item() / x1_ref.abs().max().item()
         assert err <= TOL["f64"], err
+    finally:
+        iga.iga_ops_destroy(ops)
+        iga.iga_space_destroy(space)
+
+
+@pytest.mark.parametrize("flags", [0, 1])   # default (persistent) and IGA_SOLVE_PLAIN schedules
+def test_noalloc_allocates_nothing_on_a_fresh_ops(flags):
+    space, ops = _ops("annulus64_p2")
+    try:
+        N = iga.iga_ops_info_get(ops).N
+        b = _rhs(N, 1, torch.float64)
+        # every tensor is allocated before free memory is read (torch's caching allocator
+        # would otherwise show up in the reading)
+        x0, x_ref = torch.zeros_like(b), torch.zeros_like(b)
+        xs = [torch.zeros_like(b) for _ in range(2)]
+        iga.iga_mass_solve_noalloc(ops, iga.IGA_F64, b, x0, 1, 1e-12, 2000, flags=flags)   # first call: set-up
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for x in xs:
+            iga.iga_mass_solve_noalloc(ops, iga.IGA_F64, b, x, 1, 1e-12, 2000, flags=flags)
+            torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert iga.iga_ops_info_get(ops).workspace_bytes == 0
+        iga.iga_mass_solve(ops, iga.IGA_F64, b, x_ref, 1, 1e-12, 2000, flags=flags)
+        torch.cuda.synchronize()
+        assert iga.iga_ops_info_get(ops).workspace_bytes > 0
+        scale = x_ref.abs().max().item()
+        for x in xs:
+            assert (x - x_ref).abs().max().item() <= TOL["f64"] * scale
+    finally:
+        iga.iga_ops_destroy(ops)
+        iga.iga_space_destroy(space)
+
+
+def test_noalloc_rejects_the_graph_schedule():
+    space, ops = _ops("annulus64_p2")
+    try:
+        N = iga.iga_ops_info_get(ops).N
+        b = _rhs(N, 1, torch.float64)
+        x = torch.zeros_like(b)
+        with pytest.raises(iga.IgaError) as ei:
+            iga.iga_mass_solve_noalloc(ops, iga.IGA_F64, b, x, 1, 1e-12, 2000, flags=iga.IGA_SOLVE_GRAPH)
+        assert ei.value.code == iga.IGA_ERR_ARG
+    finally:
+        iga.iga_ops_destroy(ops)
+        iga.iga_space_destroy(space)
+
+
+@pytest.mark.parametrize("entry", ["noalloc", "alloc"])
+def test_missed_tolerance_is_returned_without_statistics(entry):
+    """No statistics arrays (NULL iters_out / relres_out): the call still reports
+    IGA_ERR_NOT_CONVERGED when max_it = 2 cannot reach rtol."""
+    space, ops = _ops("annulus64_p2")
+    try:
+        N = iga.iga_ops_info_get(ops).N
+        b = _rhs(N, 1, torch.float64)
+        x = torch.zeros_like(b)
+        fn = iga.iga_mass_solve_noalloc if entry == "noalloc" else iga.iga_mass_solve
+        rc, _, _ = fn(ops, iga.IGA_F64, b, x, 1, 1e-12, 2, want_stats=False, allow_not_converged=True)
+        assert rc == iga.IGA_ERR_NOT_CONVERGED
     finally:
         iga.iga_ops_destroy(ops)
         iga.iga_space_destroy(space)
