@@ -516,6 +516,58 @@ def config2_leg(args):
     return res
 
 
+def msweep_leg(args):
+    """Mesh-dependent sampling (Sec. 5.2, Eq. MeshDependentSamplingLength) against a fixed
+    sampling length on the cube p = 2 family (sine-perturbed map, lognormal wave speed):
+    for n_el in 32, 48, 64, 96, 128, surrogate assembly with q = 2, M = 6 (the bench's)
+    and with q = 5, M = M(h) = max{1, floor(0.5 m^(1 - (p+1)/(q+1)))} (a = b = 1,
+    C = 0.5, h = 1/m, vanishing eps: the form of the paper's 2-D experiment).  Reports
+    rows/s of the assembly (device time of the second assembly on the space), samples per
+    direction, the a2 / a3 / a4 / a5 split, and the consistency error
+    max|A~ - A| / max|A| for K and M against the full-quadrature assembly of the same
+    space (IGA_TRUE_ONLY, pinned to the oracle's true matrices by the parity tests)."""
+    import torch
+
+    from paper_2004_05197_gb300 import iga
+    from paper_2004_05197_gb300 import workloads as W
+
+    def fields64(ops, which):
+        info = iga.iga_ops_info_get(ops)
+        nf = info.nK if which == iga.IGA_OP_K else info.nM
+        t = torch.empty((nf, info.N), dtype=torch.float64, device="cuda")
+        iga.iga_ops_copy_fields(ops, which, iga.IGA_F64, t)
+        return t
+
+    rows = []
+    for n in (32, 48, 64, 96, 128):
+        w = W.scaled("cube96_p2", n_el=n)
+        m = n + w["p"]
+        sp = W.make_space(w)
+        tru = iga.iga_surrogate_assemble(sp, w["p"], w["q"], 1, iga.IGA_TRUE_ONLY)
+        Mh = iga.iga_sampling_length_for_mesh(1.0 / m, w["p"], 5, 1.0, 1.0, 0.5, 1e-9)
+        for label, q, M in (("fixed", 2, 6), ("mesh_dependent", 5, Mh)):
+            o = iga.iga_surrogate_assemble(sp, w["p"], q, M, 0)
+            iga.iga_ops_destroy(o)
+            o = iga.iga_surrogate_assemble(sp, w["p"], q, M, 0)
+            info = iga.iga_ops_info_get(o)
+            err = {}
+            for name, which in (("K", iga.IGA_OP_K), ("M", iga.IGA_OP_M)):
+                a, b = fields64(o, which), fields64(tru, which)
+                err[name] = float((a - b).abs().max() / b.abs().max())
+                del a, b
+            rows.append({"n_el": n, "N": info.N, "sampling": label, "q": q, "M": M, "samples_per_dir": info.ns,
+                         "sample_rows": info.n_sample_rows, "band_elements": info.n_band_elements,
+                         "assembly_ms": info.t_total_ms, "rows_per_s": info.N / (info.t_total_ms / 1e3),
+                         "split_ms": {"band": info.t_band_ms, "sample_rows": info.t_sample_ms,
+                                      "interpolation": info.t_interp_ms, "evaluation": info.t_eval_ms},
+                         "consistency_error_K": err["K"], "consistency_error_M": err["M"]})
+            iga.iga_ops_destroy(o)
+        iga.iga_ops_destroy(tru)
+        iga.iga_space_destroy(sp)
+        torch.cuda.empty_cache()
+    return {"msweep": rows}
+
+
 def run_e2e(args, ctx):
     """Same pass through the public API from host buffers: theta, source and receiver
     positions uploaded every step, traces and the final field read back every step."""
@@ -882,6 +934,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--next-rows", action="store_true",
                     help="also measure the volume-preserving mass and the multi-patch operators")
+    ap.add_argument("--msweep", action="store_true",
+                    help="also run the sampling-length study: fixed M against M(h) over five cube meshes")
     ap.add_argument("--adjoint", action="store_true",
                     help="also run the adjoint-gradient leg (several minutes: FP64 forward / reverse sweeps)")
     ap.add_argument("--adjoint-steps", type=int, default=600)
@@ -907,6 +961,8 @@ def main():
         out["components"].update(stencil_apply_leg(ctx, args))
         if args.next_rows:
             out["components"].update(next_rows_leg(ctx, args))
+        if args.msweep:
+            out["components"].update(msweep_leg(args))
         if not args.no_compare:
             out["components"].update(fp64_forms_and_error(ctx, args))
         if args.config2_steps > 0:
