@@ -327,6 +327,17 @@ def stencil_apply_leg(ctx, args):
         gbs = (nf * 4 + 8) * N / (us * 1e-6) / 1e9
         res["stencil_apply_fp32_" + name] = {"us": us, "fields": nf, "bytes_per_row": nf * 4 + 8,
                                             "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+    # on-the-fly evaluation of the stencil functions (IGA_PATH_ONTHEFLY) on the same
+    # operator and vector: per apply the coefficient contraction over directions 1..d-1
+    # and the row kernel (surrogate-only rows from the coefficients, the rest from fields)
+    iga.iga_ops_set_path(ops, iga.IGA_PATH_ONTHEFLY)
+    L = info.m - 4 * info.p
+    deep = (L - 2 * info.p) ** info.dim / N
+    for name, which in (("K", iga.IGA_OP_K), ("M", iga.IGA_OP_M)):
+        us = _time_us(lambda: iga.iga_stencil_apply(ops, which, iga.IGA_F32, x, y, 1, stream), stream)
+        res["onthefly_apply_fp32_" + name] = {"us": us, "over_stored": us / res["stencil_apply_fp32_" + name]["us"],
+                                              "rows_from_coefficients": deep}
+    iga.iga_ops_set_path(ops, iga.IGA_PATH_AUTO)
     return res
 
 

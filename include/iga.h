@@ -224,6 +224,18 @@ int iga_stencil_apply(const iga_ops* ops, int which, int dtype, const void* x, v
 #define IGA_PATH_AUTO  0
 #define IGA_PATH_ROWS  1
 #define IGA_PATH_BRICK 2
+/* IGA_PATH_ONTHEFLY (iga_stencil_apply only, FP32 and FP64, every supported dim
+ * and p; solves run as under IGA_PATH_AUTO): the stencil functions are evaluated
+ * inside each apply from the B-spline interpolation coefficients of Sec. 3.3
+ * instead of being read from the stored fields, for every row whose whole
+ * stencil is surrogate (every interior index of the row in [3p, m-3p-1]); the
+ * other rows and the M~ diagonal are read from the stored fields.  Each apply
+ * first contracts the coefficients over directions 1..d-1 at every interior line
+ * (a table of (D-1)/2 (m-4p)^(d-1) ns values), then evaluates each entry with q+1
+ * FMAs.  Setting it allocates those tables (synchronous; IGA_ERR_ARG for an
+ * IGA_TRUE_ONLY ops or a mesh with no such row).  Results equal the stored-field
+ * apply up to rounding. */
+#define IGA_PATH_ONTHEFLY 3
 int iga_ops_set_path(iga_ops* ops, int path);
 /* Brick plan of an ops (all outputs nullable host pointers; zeros without a
  * brick form): bricks (= CTAs of a brick launch), threads per CTA, ring

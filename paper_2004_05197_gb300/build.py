@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libiga.so")
 SOURCES = ["space.cu", "assemble.cu", "apply.cu", "solve.cu", "wave.cu", "spectrum.cu", "adjoint.cu", "batch.cu",
-           "noalloc.cu", "multipatch.cu", "brick.cu"]
+           "noalloc.cu", "multipatch.cu", "brick.cu", "onthefly.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Xptxas", "-O3"]

@@ -140,6 +140,7 @@ static int apply_dispatch(const iga_ops* ops, int which, const T* F, const T* x,
 }
 
 int launch_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y, int nrhs, cudaStream_t st) {
+    if (ops->path == IGA_PATH_ONTHEFLY) return onthefly_apply(ops, which, dtype, x, y, nrhs, st);
     if (dtype == IGA_F64) {
         const double* F = which == IGA_OP_K ? ops->fK64.as<double>() : ops->fM64.as<double>();
         return apply_dispatch<double>(ops, which, F, (const double*)x, (double*)y, nrhs, st);

@@ -755,11 +755,17 @@ extern "C" int iga_surrogate_assemble(iga_space* s, int p, int q, int M, unsigne
     ops->t_total = t;
     rc = brick_prepare(ops, st);
     if (rc) return bail(rc);
+    // the interpolation coefficients and the evaluation tables stay (2 D ns^d + L (q+2)
+    // values): the on-the-fly apply evaluates the stencil functions from them
+    if (!true_only) {
+        std::swap(ops->espan.ptr, d_espan.ptr);
+        std::swap(ops->espan.bytes, d_espan.bytes);
+        std::swap(ops->evals.ptr, d_evals.ptr);
+        std::swap(ops->evals.bytes, d_evals.bytes);
+    }
     if (!(flags & IGA_KEEP_SAMPLES)) {
         ops->sK.release();
         ops->sM.release();
-        ops->cK.release();
-        ops->cM.release();
     }
     *out = ops;
     return IGA_OK;

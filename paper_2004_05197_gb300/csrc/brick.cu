@@ -405,9 +405,13 @@ using namespace iga;
 
 extern "C" int iga_ops_set_path(iga_ops* ops, int path) {
     if (!ops) return fail(IGA_ERR_ARG, "null argument");
-    if (path != IGA_PATH_AUTO && path != IGA_PATH_ROWS && path != IGA_PATH_BRICK)
-        return fail(IGA_ERR_ARG, "path must be IGA_PATH_AUTO, IGA_PATH_ROWS or IGA_PATH_BRICK");
+    if (path != IGA_PATH_AUTO && path != IGA_PATH_ROWS && path != IGA_PATH_BRICK && path != IGA_PATH_ONTHEFLY)
+        return fail(IGA_ERR_ARG, "path must be IGA_PATH_AUTO, IGA_PATH_ROWS, IGA_PATH_BRICK or IGA_PATH_ONTHEFLY");
     if (path == IGA_PATH_BRICK && !ops->brick) return fail(IGA_ERR_ARG, "no brick form (3-D, p <= 2 only)");
+    if (path == IGA_PATH_ONTHEFLY) {
+        const int rc = onthefly_prepare(ops);
+        if (rc) return rc;
+    }
     ops->path = path;
     return IGA_OK;
 }

@@ -87,6 +87,16 @@ struct BrickOps {
     BrickMaps mapK, mapM;
 };
 
+// On-the-fly evaluation of the stencil functions (onthefly.cu): per-line tables
+// G[u][line][a] of the interpolation coefficients contracted over directions 1..d-1
+// at the line's interior rows (filled by every on-the-fly apply).
+struct OtfOps {
+    int L = 0, lo = 0, ns = 0, q = 0, nf = 0;
+    long long lines = 0;                 // L^(d-1)
+    DevBuf gK64, gM64, gK32, gM32;       // [nf][lines][ns]
+    DevBuf evals32;                      // FP32 copy of the interior evaluation table
+};
+
 }  // namespace iga
 
 struct iga_space {
@@ -119,6 +129,9 @@ struct iga_ops {
     iga::DevBuf status;                      // int flags: [0] nonfinite
     iga::DevBuf work;                        // CG workspace of mass_solve (grown on demand)
     std::unique_ptr<iga::BrickOps> brick;    // brick form of the FP32 fields (3-D), else null
+    std::unique_ptr<iga::OtfOps> otf;        // tables of the on-the-fly apply (IGA_PATH_ONTHEFLY)
+    iga::DevBuf espan, evals;                // interior rows: first coefficient and the q+1 values
+                                             // of the interpolation basis at x~ (one direction)
     int path = 0;                            // IGA_PATH_*: which kernels apply the FP32 operators
     int n_band, n_samples;
     float t_sample, t_band, t_interp, t_eval, t_total;
@@ -152,6 +165,9 @@ size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs);
 int brick_prepare(iga_ops* ops, cudaStream_t st);
 bool brick_usable(const iga_ops* ops, int which);
 int brick_apply(const iga_ops* ops, int which, const float* x, float* y, cudaStream_t st);
+// onthefly.cu: y = A x with the interior stencil functions evaluated from the coefficients
+int onthefly_apply(const iga_ops* ops, int which, int dtype, const void* x, void* y, int nrhs, cudaStream_t st);
+int onthefly_prepare(iga_ops* ops);
 int spectrum_impl(const iga_ops* ops, int dtype, int k, double* lam_min, double* lam_max, cudaStream_t st);
 int wave_step_impl(iga_wave* w, int nsteps, cudaStream_t st);
 int wave_initial_state(iga_wave* w, cudaStream_t st);
