@@ -732,7 +732,8 @@ def run_adjoint(args):
     B-spline coefficients (seeded smooth perturbation of 1), q=2, M=6, dt = 0.1 h,
     8 Ricker shots at seeded positions in [0.2, 0.8]^3, 32 receivers per face
     (192), `adjoint_steps` FP64 leapfrog steps with checkpoints every 50, CG rtol
-    1e-13.  Observed traces come from a second coefficient field through the same
+    1e-13, CG start of order `cg_guess` in every sweep.  Observed traces come from a
+    second coefficient field through the same
     forward path.  Timed: J and its gradient through the torch.autograd.Function
     (assembly, forward with checkpoints, reverse sweep with recomputation).
     Check: central difference with eps = 1e-6 along one seeded direction against
@@ -754,7 +755,8 @@ def run_adjoint(args):
                               theta=inputs.colex(theta_obs), n_theta=12, theta_degree=3)
     ops = iga.iga_surrogate_assemble(sp, 2, 2, 6)
     wv = iga.iga_wave_create(ops, nshot, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1, rec_pos=rec,
-                             nsteps_max=nsteps, cg_rtol=1e-13, cg_max_it=5000, cfl_check=1)
+                             nsteps_max=nsteps, cg_rtol=1e-13, cg_max_it=5000, cfl_check=1,
+                             cg_guess=args.cg_guess)
     iga.iga_wave_step(wv, nsteps)
     obs = iga.iga_wave_traces(wv, nshot, len(rec), nsteps)
     st = iga.iga_wave_stats_get(wv)
@@ -764,7 +766,7 @@ def run_adjoint(args):
     iga.iga_space_destroy(sp)
     problem = dict(dim=3, p=2, n_el=n_el, map_kind=iga.IGA_MAP_CUBE_SINE, map_param=0.1, q=2, M=6, dt=dt,
                    nsteps=nsteps, checkpoint_every=50, src_pos=src, rec_pos=rec, obs=obs, f0=10.0, t0=0.1,
-                   cg_rtol=1e-13)
+                   cg_rtol=1e-13, cg_guess=args.cg_guess)
     th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -782,7 +784,7 @@ def run_adjoint(args):
     fd = (Jp - Jm) / (2 * eps)
     gv = float(np.sum(g * v))
     return {"adjoint_workload": ("cube 64^3 p=2, 12^3 theta, 8 shots x %d FP64 steps, checkpoints every 50, "
-                                 "192 receivers" % nsteps),
+                                 "192 receivers, CG start order %d" % (nsteps, args.cg_guess)),
             "adjoint_gradient_s": t_grad, "adjoint_shot_steps_per_s": nshot * nsteps / t_grad,
             "adjoint_J": float(J), "adjoint_grad_dot_v": gv, "adjoint_central_fd": fd,
             "adjoint_fd_rel_error": abs(gv - fd) / max(abs(gv), 1e-300),

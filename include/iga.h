@@ -353,7 +353,9 @@ typedef struct iga_wave_desc {
                                    allow (a^{-1} = 0 at n = 0, order min(K, n - 1) after).  Only
                                    the starting point of the CG changes; every solve still runs
                                    to cg_rtol.  K extra acceleration vectors per shot are kept.
-                                   wave_adjoint runs its forward sweeps with order 0 */
+                                   wave_adjoint uses the same order in its forward and
+                                   recomputed sweeps (checkpoints keep the K accelerations)
+                                   and in reverse time for its adjoint solves */
 } iga_wave_desc;
 
 int iga_wave_create(const iga_ops* ops, const iga_wave_desc* desc, iga_wave** out);
@@ -419,8 +421,8 @@ int iga_batch_partition(const iga_batch* batch, int* blocks_out);
 
 /* ---- adjoint ------------------------------------------------------------
  * wave_adjoint: restarts the wave (FP64 only) from its initial condition, runs
- * nsteps leapfrog steps with checkpoints (u^n, u^{n-1}, a^{n-1}) every
- * checkpoint_every steps, evaluates the receiver misfit
+ * nsteps leapfrog steps with checkpoints (u^n, u^{n-1}, a^{n-1} and the cg_guess
+ * older accelerations) every checkpoint_every steps, evaluates the receiver misfit
  *     J = dt/2 sum_shots sum_receivers sum_{n=1..nsteps} (d^n - obs^n)^2
  * and, if grad_theta != NULL, its gradient with respect to the B-spline
  * coefficients theta of the wave speed (space created with IGA_COEF_BSPLINE) by

@@ -12,9 +12,13 @@
 // K~ is stored as its upper triangle S_delta[i] = K~(i, i+Delta) with the
 // diagonal minus the row sum, so the gradient of a stored value is
 //   G_delta[i] = sum_m c_m dt^2 (nu_i - nu_{i+Delta}) (u_i - u_{i+Delta}).
-// Checkpoints: (u^n, u^{n-1}, a^{n-1}) every C steps; each segment is recomputed
-// from its checkpoint (bitwise identical: same CG warm start) and then swept
-// backwards.
+// Checkpoints: (u^n, u^{n-1}, a^{n-1}) and, with a CG start of order K > 0, the K
+// older accelerations a^{n-2} .. a^{n-1-K}, every C steps; each segment is
+// recomputed from its checkpoint (bitwise identical: the same CG starts) and then
+// swept backwards.  The reverse-sweep solves M~ nu^m = ubar^{m+1} start from the
+// same polynomial extrapolation, in reverse time, of nu^{m+1}, nu^{m+2}, .. (order
+// up to K; only the starting point of each solve changes, every solve still runs
+// to cg_rtol).
 //
 // Back through the assembly (every stored value is linear in true entries):
 //   true slots        S = K_ij                                 (band elements)
@@ -53,6 +57,26 @@ __global__ void grad_accum_kernel(double* __restrict__ G, long long pitch, const
             G[(size_t)f * pitch + i] += c * acc;
         }
     }
+}
+
+// x = sum_{j <= k} c_j h_j with c_j = (-1)^j C(k+1, j+1): the degree-k polynomial
+// through h_0 .. h_k evaluated one step further (start of the next adjoint solve).
+struct NuGuess {
+    const double* h[IGA_CG_GUESS_MAX + 1];
+    double c[IGA_CG_GUESS_MAX + 1];
+    int k;
+};
+__global__ void adj_guess_kernel(double* x, NuGuess g, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int j = 0; j <= g.k; ++j) v += g.c[j] * g.h[j][i];
+        x[i] = v;
+    }
+}
+static double binom_coeff(int k, int j) {   // (-1)^j C(k+1, j+1)
+    double b = 1.0;
+    for (int t = 1; t <= j + 1; ++t) b = b * (k + 2 - t) / t;
+    return (j & 1) ? -b : b;
 }
 
 // ubar_s += scale sum_rec res[s][rec] R_rec^T (one thread per shot: deterministic)
@@ -302,15 +326,24 @@ static int adjoint_dp(iga_wave* w, int nsteps, int ckpt, const double* obs, doub
     const int K = (nsteps + ckpt - 1) / ckpt;
     const int ugrid = (int)std::min<long long>((vec + 255) / 256, 152 * 16);
     int rc;
-    // ---- forward with checkpoints (u^n, u^{n-1}, a^{n-1}) at n = k C
+    // ---- forward with checkpoints (u^n, u^{n-1}, a^{n-1}, a^{n-2} .. a^{n-1-Kg}) at n = k C
+    const int Kg = w->desc.cg_guess;
+    const int nck = 3 + Kg;   // vectors per checkpoint
     DevBuf ckb;
-    if ((rc = ckb.alloc(sizeof(double) * vec * 3 * K))) return rc;
+    if ((rc = ckb.alloc(sizeof(double) * vec * nck * K))) return rc;
     if ((rc = wave_initial_state(w, st))) return rc;
+    auto ck_vectors = [&](int k, void** v) {
+        v[0] = w->u.ptr;
+        v[1] = w->uprev.ptr;
+        v[2] = w->a.ptr;
+        for (int j = 0; j < Kg; ++j) v[3 + j] = w->ah[j].ptr;
+        return ckb.as<double>() + (size_t)nck * k * vec;
+    };
     for (int k = 0; k < K; ++k) {
-        double* c = ckb.as<double>() + (size_t)3 * k * vec;
-        IGA_CUDA(cudaMemcpyAsync(c, w->u.ptr, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
-        IGA_CUDA(cudaMemcpyAsync(c + vec, w->uprev.ptr, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
-        IGA_CUDA(cudaMemcpyAsync(c + 2 * vec, w->a.ptr, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
+        void* v[3 + IGA_CG_GUESS_MAX];
+        double* c = ck_vectors(k, v);
+        for (int j = 0; j < nck; ++j)
+            IGA_CUDA(cudaMemcpyAsync(c + (size_t)j * vec, v[j], sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
         if ((rc = wave_step_impl(w, std::min(ckpt, nsteps - k * ckpt), st))) return rc;
     }
     // ---- misfit and residuals res[m][s][rec] = d^m - d_obs^m (m = 1..N, traces index m-1)
@@ -339,8 +372,14 @@ static int adjoint_dp(iga_wave* w, int nsteps, int ckpt, const double* obs, doub
     double* ub1 = vb.as<double>();   // ubar^{m+1}
     double* ub2 = ub1 + vec;         // ubar^{m+2}
     double* ubn = ub2 + vec;         // ubar^m
-    double* nu = ubn + vec;
+    double* nu = ubn + vec;          // nu^m (the solve's iterate)
     double* y = nu + vec;
+    // nu^{m+1}, nu^{m+2}, .. for the extrapolated start of the reverse solves
+    DevBuf nhb;
+    if (Kg > 0 && (rc = nhb.alloc(sizeof(double) * vec * (Kg + 1)))) return rc;
+    std::vector<double*> nuh;
+    for (int j = 0; j <= Kg && Kg > 0; ++j) nuh.push_back(nhb.as<double>() + (size_t)j * vec);
+    int n_hist = 0;   // nu vectors solved so far (reverse time)
     // ubar^N = dt R^T res^N
     adj_inject_kernel<<<(nshot + 31) / 32, 32, 0, st>>>(ub1, w->rec_idx.as<int>(), w->rec_w.as<double>(),
                                                         dres.as<double>() + (size_t)nsteps * nshot * nrec, nshot,
@@ -349,10 +388,12 @@ static int adjoint_dp(iga_wave* w, int nsteps, int ckpt, const double* obs, doub
     const int grid = (int)std::min<long long>((N + 255) / 256, 152 * 8);
     for (int k = K - 1; k >= 0; --k) {
         const int n0 = k * ckpt, n1 = std::min(n0 + ckpt, nsteps);
-        const double* c = ckb.as<double>() + (size_t)3 * k * vec;
-        IGA_CUDA(cudaMemcpyAsync(w->u.ptr, c, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
-        IGA_CUDA(cudaMemcpyAsync(w->uprev.ptr, c + vec, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
-        IGA_CUDA(cudaMemcpyAsync(w->a.ptr, c + 2 * vec, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
+        {
+            void* v[3 + IGA_CG_GUESS_MAX];
+            const double* c = ck_vectors(k, v);
+            for (int j = 0; j < nck; ++j)
+                IGA_CUDA(cudaMemcpyAsync(v[j], c + (size_t)j * vec, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
+        }
         w->step = n0;
         IGA_CUDA(cudaMemcpyAsync(seg.ptr, w->u.ptr, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
         for (int j = 1; j < n1 - n0; ++j) {
@@ -361,9 +402,28 @@ static int adjoint_dp(iga_wave* w, int nsteps, int ckpt, const double* obs, doub
                                      cudaMemcpyDeviceToDevice, st));
         }
         for (int m = n1 - 1; m >= n0; --m) {
+            if (Kg > 0 && n_hist >= 2) {
+                // extrapolated start from nu^{m+1} .. nu^{m+1+kk}
+                NuGuess gs;
+                gs.k = std::min(Kg, n_hist - 1);
+                for (int j = 0; j <= gs.k; ++j) {
+                    gs.h[j] = nuh[j];
+                    gs.c[j] = binom_coeff(gs.k, j);
+                }
+                adj_guess_kernel<<<ugrid, 256, 0, st>>>(nu, gs, (long long)vec);
+                IGA_LAUNCH_CHECK("adj_guess_kernel");
+            }
             rc = mass_solve_impl(ops, IGA_F64, ub1, nu, N, nshot, w->desc.cg_rtol, w->desc.cg_max_it, 0, nullptr,
                                  nullptr, st, w->work.ptr, w->work.bytes, nullptr, nullptr);
             if (rc) return rc;
+            if (Kg > 0) {
+                // nuh[0] <- nu^m, older ones shift (the oldest buffer is reused)
+                double* oldest = nuh[Kg];
+                for (int j = Kg; j > 0; --j) nuh[j] = nuh[j - 1];
+                nuh[0] = oldest;
+                IGA_CUDA(cudaMemcpyAsync(nuh[0], nu, sizeof(double) * vec, cudaMemcpyDeviceToDevice, st));
+                n_hist = std::min(n_hist + 1, Kg + 1);
+            }
             grad_accum_kernel<DIM, P><<<grid, 256, 0, st>>>(G.as<double>(), ops->pitch, nu,
                                                             seg.as<double>() + (size_t)(m - n0) * vec, nshot, N,
                                                             (int)N, ops->m, (m == 0 ? 0.5 : 1.0) * dt2);
@@ -503,15 +563,9 @@ extern "C" int iga_wave_adjoint(iga_wave* w, int nsteps, int checkpoint_every, c
         return fail(IGA_ERR_ARG, "the gradient is taken with respect to a B-spline wave speed");
     cudaStream_t st = (cudaStream_t)stream;
     const int d = sp->dim, p = sp->p;
-    // The forward and the recomputed segments start every solve from a^{n-1}
-    // (cg_guess 0), so a checkpoint (u^n, u^{n-1}, a^{n-1}) restarts a segment
-    // exactly; the wave's own setting is restored on return.
-    struct GuessOff {
-        iga_wave* w;
-        int saved;
-        ~GuessOff() { w->desc.cg_guess = saved; }
-    } guess_off{w, w->desc.cg_guess};
-    w->desc.cg_guess = 0;
+    // The forward and the recomputed segments use the wave's CG start (cg_guess);
+    // the checkpoints carry the acceleration history it needs, so every segment
+    // restarts exactly.
     int rc;
     if (d == 2 && p == 1) rc = adjoint_dp<2, 1>(w, nsteps, checkpoint_every, obs, J_out, grad_theta, st);
     else if (d == 2 && p == 2) rc = adjoint_dp<2, 2>(w, nsteps, checkpoint_every, obs, J_out, grad_theta, st);

@@ -32,13 +32,13 @@ def small_case():
                 obs=d_obs, n_el=10)
 
 
-def gpu_adjoint(case, theta, want_grad=True, ckpt=50, rtol=1e-14):
+def gpu_adjoint(case, theta, want_grad=True, ckpt=50, rtol=1e-14, guess=0):
     sp = iga.iga_space_create(3, 2, case["n_el"], iga.IGA_MAP_CUBE_SINE, 0.1, iga.IGA_COEF_BSPLINE, 0.0,
                               theta=inputs.colex(theta), n_theta=theta.shape[0], theta_degree=3)
     ops = iga.iga_surrogate_assemble(sp, 2, case["q"], case["M"])
     w = iga.iga_wave_create(ops, len(case["src"]), iga.IGA_F64, case["dt"], src_pos=case["src"], f0=10.0, t0=0.1,
                             rec_pos=case["rec"], nsteps_max=case["nsteps"], cg_rtol=rtol, cg_max_it=5000,
-                            cfl_check=0)
+                            cfl_check=0, cg_guess=guess)
     J, g = iga.iga_wave_adjoint(w, case["nsteps"], ckpt, case["obs"], n_theta_total=theta.size if want_grad else 0)
     iga.iga_wave_destroy(w)
     iga.iga_ops_destroy(ops)
@@ -55,10 +55,12 @@ def test_adjoint_misfit_matches_oracle():
     assert abs(J_gpu - J_ora) <= 1e-10 * J_ora
 
 
-@pytest.mark.parametrize("seed", [31, 32])
-def test_adjoint_gradient_matches_oracle_tangent(seed):
+@pytest.mark.parametrize("seed,guess", [(31, 0), (32, 0), (31, 3)])
+def test_adjoint_gradient_matches_oracle_tangent(seed, guess):
+    """guess: the wave's CG start order (3: the extrapolated start in the forward,
+    recomputed and reverse sweeps; only where each solve starts changes)."""
     c = small_case()
-    _, g = gpu_adjoint(c, c["theta"])
+    _, g = gpu_adjoint(c, c["theta"], guess=guess)
     v = np.random.default_rng(seed).standard_normal(c["theta"].shape)
     jt = tangent(c["base"], c["theta"], v, c["q"], c["M"], c["dt"], c["nsteps"], c["shots"], list(c["rec"]),
                  c["obs"])
@@ -67,11 +69,22 @@ def test_adjoint_gradient_matches_oracle_tangent(seed):
     assert abs(gv - jt) <= 1e-7 * abs(jt)
 
 
-def test_adjoint_is_independent_of_checkpoint_spacing():
+@pytest.mark.parametrize("guess", [0, 3])
+def test_adjoint_is_independent_of_checkpoint_spacing(guess):
+    """With guess = 3 the checkpoints carry the acceleration history, so a segment
+    recomputed from a checkpoint repeats the forward sweep exactly."""
     c = small_case()
-    _, g1 = gpu_adjoint(c, c["theta"], ckpt=3)
-    _, g2 = gpu_adjoint(c, c["theta"], ckpt=100)
+    _, g1 = gpu_adjoint(c, c["theta"], ckpt=3, guess=guess)
+    _, g2 = gpu_adjoint(c, c["theta"], ckpt=100, guess=guess)
     assert np.abs(g1 - g2).max() <= 1e-12 * np.abs(g2).max()
+
+
+def test_adjoint_cg_start_changes_only_rounding():
+    c = small_case()
+    J0, g0 = gpu_adjoint(c, c["theta"], guess=0)
+    J3, g3 = gpu_adjoint(c, c["theta"], guess=3)
+    assert abs(J3 - J0) <= 1e-11 * J0
+    assert np.abs(g3 - g0).max() <= 1e-9 * np.abs(g0).max()
 
 
 def test_autograd_function_returns_the_adjoint_gradient():
