@@ -732,7 +732,9 @@ def run_adjoint(args):
     B-spline coefficients (seeded smooth perturbation of 1), q=2, M=6, dt = 0.1 h,
     8 Ricker shots at seeded positions in [0.2, 0.8]^3, 32 receivers per face
     (192), `adjoint_steps` FP64 leapfrog steps with checkpoints every 50, CG rtol
-    1e-13, CG start of order `cg_guess` in every sweep.  Observed traces come from a
+    1e-13, CG start of order `cg_guess` in every sweep, FP64 solves by iterative
+    refinement (FP64 residual, FP32 Jacobi-PCG corrections; --adjoint-cg: FP64
+    Jacobi-PCG throughout).  Observed traces come from a
     second coefficient field through the same
     forward path.  Timed: J and its gradient through the torch.autograd.Function
     (assembly, forward with checkpoints, reverse sweep with recomputation).
@@ -754,9 +756,10 @@ def run_adjoint(args):
     sp = iga.iga_space_create(3, 2, n_el, iga.IGA_MAP_CUBE_SINE, 0.1, iga.IGA_COEF_BSPLINE, 0.0,
                               theta=inputs.colex(theta_obs), n_theta=12, theta_degree=3)
     ops = iga.iga_surrogate_assemble(sp, 2, 2, 6)
+    sflags = 0 if args.adjoint_cg else iga.IGA_SOLVE_REFINE
     wv = iga.iga_wave_create(ops, nshot, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1, rec_pos=rec,
                              nsteps_max=nsteps, cg_rtol=1e-13, cg_max_it=5000, cfl_check=1,
-                             cg_guess=args.cg_guess)
+                             cg_guess=args.cg_guess, solve_flags=sflags)
     iga.iga_wave_step(wv, nsteps)
     obs = iga.iga_wave_traces(wv, nshot, len(rec), nsteps)
     st = iga.iga_wave_stats_get(wv)
@@ -766,7 +769,7 @@ def run_adjoint(args):
     iga.iga_space_destroy(sp)
     problem = dict(dim=3, p=2, n_el=n_el, map_kind=iga.IGA_MAP_CUBE_SINE, map_param=0.1, q=2, M=6, dt=dt,
                    nsteps=nsteps, checkpoint_every=50, src_pos=src, rec_pos=rec, obs=obs, f0=10.0, t0=0.1,
-                   cg_rtol=1e-13, cg_guess=args.cg_guess)
+                   cg_rtol=1e-13, cg_guess=args.cg_guess, solve_flags=sflags)
     th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -784,7 +787,9 @@ def run_adjoint(args):
     fd = (Jp - Jm) / (2 * eps)
     gv = float(np.sum(g * v))
     return {"adjoint_workload": ("cube 64^3 p=2, 12^3 theta, 8 shots x %d FP64 steps, checkpoints every 50, "
-                                 "192 receivers, CG start order %d" % (nsteps, args.cg_guess)),
+                                 "192 receivers, CG start order %d, %s" %
+                                 (nsteps, args.cg_guess, "FP64 Jacobi-PCG" if args.adjoint_cg else
+                                  "FP64 solves by refinement with FP32 Jacobi-PCG corrections")),
             "adjoint_gradient_s": t_grad, "adjoint_shot_steps_per_s": nshot * nsteps / t_grad,
             "adjoint_J": float(J), "adjoint_grad_dot_v": gv, "adjoint_central_fd": fd,
             "adjoint_fd_rel_error": abs(gv - fd) / max(abs(gv), 1e-300),
@@ -952,6 +957,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="also run the adjoint-gradient leg (several minutes: FP64 forward / reverse sweeps)")
     ap.add_argument("--adjoint-steps", type=int, default=600)
+    ap.add_argument("--adjoint-cg", action="store_true",
+                    help="adjoint leg with FP64 Jacobi-PCG solves instead of refinement")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

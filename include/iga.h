@@ -93,6 +93,13 @@ extern "C" {
                                  graph whose conditional WHILE node iterates until the device decides
                                  convergence (no grid barrier, no host round trip); falls back to
                                  the persistent schedule when the stream is being captured */
+#define IGA_SOLVE_REFINE  4u  /* FP64 solves only: iterative refinement, the FP64 residual
+                                 b - M~x with the FP64 fields, the correction from the FP32
+                                 Jacobi-PCG on the FP32 fields, x += d in FP64, until the FP64
+                                 residual meets rtol (same stopping rule as the FP64 solve).
+                                 Synchronises the stream once per refinement; iters_out
+                                 counts the FP32 CG iterations.  Combines with
+                                 IGA_SOLVE_PLAIN / IGA_SOLVE_GRAPH for the inner solves */
 
 /* wave initial conditions */
 #define IGA_INIT_ZERO         0
@@ -288,7 +295,8 @@ int iga_mass_solve(const iga_ops* ops, int dtype, const void* b, void* x, int nr
  * device that loads the library does.  The call synchronises the stream (the
  * solver status is always read back into host memory).
  * IGA_SOLVE_GRAPH is rejected (IGA_ERR_ARG): that schedule instantiates a CUDA
- * graph per call, which may reserve device resources.
+ * graph per call, which may reserve device resources; so is IGA_SOLVE_REFINE,
+ * whose extra vectors the fixed array is not sized for.
  * Sharing: all calls on a device use the same array, so calls that overlap in
  * time (different streams or host threads) race and corrupt one another;
  * the caller must serialise them (e.g. one stream). */

@@ -29,7 +29,8 @@ class SurrogateWaveMisfit(torch.autograd.Function):
                                    f0=problem.get("f0", 10.0), t0=problem.get("t0", 0.1),
                                    rec_pos=problem["rec_pos"], nsteps_max=nsteps,
                                    cg_rtol=problem.get("cg_rtol", 1e-13), cg_max_it=problem.get("cg_max_it", 5000),
-                                   cfl_check=0, cg_guess=problem.get("cg_guess", 0))
+                                   cfl_check=0, cg_guess=problem.get("cg_guess", 0),
+                                   solve_flags=problem.get("solve_flags", 0))
         want = ctx.needs_input_grad[0]
         J, g = iga.iga_wave_adjoint(wave, nsteps, problem.get("checkpoint_every", 50), problem["obs"],
                                     n_theta_total=flat.size if want else 0)

@@ -413,8 +413,9 @@ static int adjoint_dp(iga_wave* w, int nsteps, int ckpt, const double* obs, doub
                 adj_guess_kernel<<<ugrid, 256, 0, st>>>(nu, gs, (long long)vec);
                 IGA_LAUNCH_CHECK("adj_guess_kernel");
             }
-            rc = mass_solve_impl(ops, IGA_F64, ub1, nu, N, nshot, w->desc.cg_rtol, w->desc.cg_max_it, 0, nullptr,
-                                 nullptr, st, w->work.ptr, w->work.bytes, nullptr, nullptr);
+            rc = mass_solve_impl(ops, IGA_F64, ub1, nu, N, nshot, w->desc.cg_rtol, w->desc.cg_max_it,
+                                 w->desc.solve_flags, nullptr, nullptr, st, w->work.ptr, w->work.bytes, nullptr,
+                                 nullptr);
             if (rc) return rc;
             if (Kg > 0) {
                 // nuh[0] <- nu^m, older ones shift (the oldest buffer is reused)

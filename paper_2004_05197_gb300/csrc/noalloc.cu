@@ -46,6 +46,8 @@ extern "C" int iga_mass_solve_noalloc(const iga_ops* ops, int dtype, const void*
     // the graph schedule builds and instantiates a CUDA graph per call, which may
     // reserve device resources: not offered here
     if (flags & IGA_SOLVE_GRAPH) return fail(IGA_ERR_ARG, "mass_solve_noalloc does not take IGA_SOLVE_GRAPH");
+    // the fixed array is sized for the plain solves, not for a refinement chunk
+    if (flags & IGA_SOLVE_REFINE) return fail(IGA_ERR_ARG, "mass_solve_noalloc does not take IGA_SOLVE_REFINE");
     const size_t need = mass_solve_work_bytes_nrhs(ops, dtype, nrhs);
     if (need > (size_t)IGA_NOALLOC_SCRATCH_BYTES)
         return fail(IGA_ERR_ARG, "mass_solve_noalloc: CG workspace of " + std::to_string(need) +

@@ -946,10 +946,151 @@ static int work_blocks() {
     return std::max(1, sms) * std::max(kCgMaxBlocksPerSM, 16);
 }
 
+// FP64 workspace also holds an IGA_SOLVE_REFINE chunk: FP64 residual, FP32 residual
+// and FP32 correction of up to 4 right-hand sides, then the FP32 CG workspace.
+static size_t refine_extra_bytes(long long N) { return (size_t)16 * 4 * (size_t)N + 3 * 256; }
+
 size_t mass_solve_work_bytes(const iga_ops* ops, int dtype, int nrhs) {
     (void)nrhs;
     const int nb = work_blocks();
-    return carve_bytes(dtype == IGA_F64 ? 8 : 4, (ops->N + 3) / 4 * 4, 4, nb);   // R = 4 is the largest chunk
+    const long long N4 = (ops->N + 3) / 4 * 4;
+    const size_t plain = carve_bytes(dtype == IGA_F64 ? 8 : 4, N4, 4, nb);   // R = 4 is the largest chunk
+    if (dtype != IGA_F64) return plain;
+    return std::max(plain, refine_extra_bytes(ops->N) + carve_bytes(4, N4, 4, nb));
+}
+
+// ---------------------------------------------------------------- IGA_SOLVE_REFINE
+// FP64 solve by iterative refinement: r = b - M~x with the FP64 fields, correction
+// d from the FP32 Jacobi-PCG on the FP32 fields (the fast kernels), x += d in FP64,
+// until ||b - M~x||_2 <= rtol ||b||_2 for every right-hand side (the stopping rule of
+// the FP64 solve, on the FP64 residual).  Each refinement gains about the digits of
+// the FP32 solve, up to cond(M~) times the FP32 rounding of the fields.
+__global__ void refine_norm_kernel(const double* __restrict__ v, long long ld, int N, double* out) {
+    __shared__ double ws[32];
+    const double* x = v + (size_t)blockIdx.x * ld;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) acc += x[i] * x[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        out[blockIdx.x] = t;
+    }
+}
+
+// r64 holds M~x on entry: r64 = b - M~x; r32 = r64 in FP32 (0 for converged columns)
+__global__ void refine_residual_kernel(const double* __restrict__ b, double* __restrict__ r64,
+                                       float* __restrict__ r32, long long N, int R, unsigned done_mask) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)R * N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / N);
+        const double r = b[idx] - r64[idx];
+        r64[idx] = r;
+        r32[idx] = ((done_mask >> s) & 1u) ? 0.f : (float)r;
+    }
+}
+
+__global__ void refine_update_kernel(double* __restrict__ x, const float* __restrict__ d, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+static int refine_chunk(const iga_ops* ops, const double* b, double* x, int R, double rtol, int max_it,
+                        unsigned flags, int* iters_h, double* relres_h, bool* nc, cudaStream_t st, void* work,
+                        size_t work_bytes, long long* tot_iters) {
+    const long long N = ops->N;
+    char* base = (char*)work;
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    double* r64 = (double*)base;
+    float* r32 = (float*)(base + up(sizeof(double) * 4 * N));
+    float* d32 = (float*)((char*)r32 + up(sizeof(float) * 4 * N));
+    double* nrm = (double*)((char*)d32 + up(sizeof(float) * 4 * N));
+    char* inner = (char*)nrm + 256;
+    if ((size_t)(inner - base) > work_bytes) return fail(IGA_ERR_ARG, "CG workspace too small");
+    const size_t inner_bytes = work_bytes - (size_t)(inner - base);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((R * N + 255) / 256, 152 * 16));
+    double bn[4], rn[4];
+    refine_norm_kernel<<<R, 1024, 0, st>>>(b, N, (int)N, nrm);
+    IGA_LAUNCH_CHECK("refine_norm_kernel");
+    IGA_CUDA(cudaMemcpyAsync(bn, nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r) {
+        bn[r] = std::sqrt(bn[r]);
+        iters_h[r] = 0;
+        if (!(bn[r] > 0.0)) IGA_CUDA(cudaMemsetAsync(x + (size_t)r * N, 0, sizeof(double) * N, st));
+    }
+    constexpr int kMaxRefine = 12;
+    unsigned done = 0;
+    for (int k = 0; k <= kMaxRefine; ++k) {
+        int rc = launch_apply(ops, IGA_OP_M, IGA_F64, x, r64, R, st);
+        if (rc) return rc;
+        refine_residual_kernel<<<grid, 256, 0, st>>>(b, r64, r32, N, R, done);
+        IGA_LAUNCH_CHECK("refine_residual_kernel");
+        refine_norm_kernel<<<R, 1024, 0, st>>>(r64, N, (int)N, nrm);
+        IGA_LAUNCH_CHECK("refine_norm_kernel");
+        IGA_CUDA(cudaMemcpyAsync(rn, nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        IGA_CUDA(cudaStreamSynchronize(st));
+        double target = 1.0;
+        for (int r = 0; r < R; ++r) {
+            rn[r] = std::sqrt(rn[r]);
+            relres_h[r] = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
+            if (!(bn[r] > 0.0) || (rtol > 0.0 && relres_h[r] <= rtol)) done |= 1u << r;
+            else target = std::min(target, rtol * bn[r] / rn[r]);
+        }
+        if (done == (1u << R) - 1 || k == kMaxRefine) break;
+        // the FP32 correction: to 1e-6, or to what is left of the tolerance
+        const double inner_rtol = std::max(1e-6, std::min(0.1, 0.5 * target));
+        IGA_CUDA(cudaMemsetAsync(d32, 0, sizeof(float) * R * N, st));
+        int it32[4];
+        double rr32[4];
+        rc = mass_solve_impl(ops, IGA_F32, r32, d32, N, R, inner_rtol, max_it, flags, it32, rr32, st, inner,
+                             inner_bytes, nullptr, nullptr);
+        if (rc && rc != IGA_ERR_NOT_CONVERGED) return rc;
+        for (int r = 0; r < R; ++r) {
+            iters_h[r] += it32[r];
+            *tot_iters += it32[r];
+        }
+        refine_update_kernel<<<grid, 256, 0, st>>>(x, d32, (long long)R * N);
+        IGA_LAUNCH_CHECK("refine_update_kernel");
+    }
+    for (int r = 0; r < R; ++r)
+        if (rtol > 0.0 && bn[r] > 0.0 && relres_h[r] > rtol) *nc = true;
+    return IGA_OK;
+}
+
+static int refine_solve(const iga_ops* ops, const double* b, double* x, long long ld, int nrhs, double rtol,
+                        int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st, void* work,
+                        size_t work_bytes, long long* iter_acc, int* status_acc) {
+    if (ld != ops->N) return fail(IGA_ERR_ARG, "IGA_SOLVE_REFINE needs vectors of leading dimension N");
+    bool nc = false;
+    long long tot = 0;
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+        const int R = std::min(4, nrhs - r0);
+        int it[4];
+        double rel[4];
+        const int rc = refine_chunk(ops, b + (size_t)r0 * ld, x + (size_t)r0 * ld, R, rtol, max_it, flags, it, rel,
+                                    &nc, st, work, work_bytes, &tot);
+        if (rc) return rc;
+        for (int r = 0; r < R; ++r) {
+            if (iters_out) iters_out[r0 + r] = it[r];
+            if (relres_out) relres_out[r0 + r] = rel[r];
+        }
+    }
+    if (iter_acc || status_acc) {
+        // fold the host-side counts into the caller's device accumulators
+        long long acc_h = 0;
+        int st_h = 0;
+        if (iter_acc) IGA_CUDA(cudaMemcpy(&acc_h, iter_acc, sizeof(acc_h), cudaMemcpyDeviceToHost));
+        if (status_acc) IGA_CUDA(cudaMemcpy(&st_h, status_acc, sizeof(st_h), cudaMemcpyDeviceToHost));
+        acc_h += tot;
+        if (nc) st_h |= 8;
+        if (iter_acc) IGA_CUDA(cudaMemcpy(iter_acc, &acc_h, sizeof(acc_h), cudaMemcpyHostToDevice));
+        if (status_acc) IGA_CUDA(cudaMemcpy(status_acc, &st_h, sizeof(st_h), cudaMemcpyHostToDevice));
+    }
+    if (nc && (iters_out || relres_out)) return fail(IGA_ERR_NOT_CONVERGED, "refinement reached its limit before rtol");
+    return IGA_OK;
 }
 
 // Workspace for exactly the chunks pcg_typed runs for nrhs right-hand sides
@@ -962,6 +1103,9 @@ size_t mass_solve_work_bytes_nrhs(const iga_ops* ops, int dtype, int nrhs) {
 int mass_solve_impl(const iga_ops* ops, int dtype, const void* b, void* x, long long ld, int nrhs, double rtol,
                     int max_it, unsigned flags, int* iters_out, double* relres_out, cudaStream_t st, void* work,
                     size_t work_bytes, long long* iter_acc, int* status_acc) {
+    if (dtype == IGA_F64 && (flags & IGA_SOLVE_REFINE))
+        return refine_solve(ops, (const double*)b, (double*)x, ld, nrhs, rtol, max_it, flags & ~IGA_SOLVE_REFINE,
+                            iters_out, relres_out, st, work, work_bytes, iter_acc, status_acc);
     bool nc = false;
     const bool want = iters_out || relres_out;
     std::vector<int> it_h(nrhs);

@@ -27,7 +27,7 @@ IGA_COEF_CONST, IGA_COEF_SINCOS, IGA_COEF_BSPLINE = 0, 1, 2
 IGA_F32, IGA_F64 = 0, 1
 IGA_OP_K, IGA_OP_M = 0, 1
 IGA_TRUE_ONLY, IGA_KEEP_SAMPLES, IGA_MASS_VOLUME_PRESERVING = 1, 2, 4
-IGA_SOLVE_PLAIN, IGA_SOLVE_GRAPH = 1, 2
+IGA_SOLVE_PLAIN, IGA_SOLVE_GRAPH, IGA_SOLVE_REFINE = 1, 2, 4
 IGA_INIT_ZERO, IGA_INIT_GAUSS_PULSE = 0, 1
 IGA_PATH_AUTO, IGA_PATH_ROWS, IGA_PATH_BRICK, IGA_PATH_ONTHEFLY = 0, 1, 2, 3
 

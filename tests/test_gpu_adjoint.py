@@ -32,13 +32,13 @@ def small_case():
                 obs=d_obs, n_el=10)
 
 
-def gpu_adjoint(case, theta, want_grad=True, ckpt=50, rtol=1e-14, guess=0):
+def gpu_adjoint(case, theta, want_grad=True, ckpt=50, rtol=1e-14, guess=0, flags=0):
     sp = iga.iga_space_create(3, 2, case["n_el"], iga.IGA_MAP_CUBE_SINE, 0.1, iga.IGA_COEF_BSPLINE, 0.0,
                               theta=inputs.colex(theta), n_theta=theta.shape[0], theta_degree=3)
     ops = iga.iga_surrogate_assemble(sp, 2, case["q"], case["M"])
     w = iga.iga_wave_create(ops, len(case["src"]), iga.IGA_F64, case["dt"], src_pos=case["src"], f0=10.0, t0=0.1,
                             rec_pos=case["rec"], nsteps_max=case["nsteps"], cg_rtol=rtol, cg_max_it=5000,
-                            cfl_check=0, cg_guess=guess)
+                            cfl_check=0, cg_guess=guess, solve_flags=flags)
     J, g = iga.iga_wave_adjoint(w, case["nsteps"], ckpt, case["obs"], n_theta_total=theta.size if want_grad else 0)
     iga.iga_wave_destroy(w)
     iga.iga_ops_destroy(ops)
@@ -79,11 +79,12 @@ def test_adjoint_is_independent_of_checkpoint_spacing(guess):
     assert np.abs(g1 - g2).max() <= 1e-12 * np.abs(g2).max()
 
 
-def test_adjoint_cg_start_changes_only_rounding():
+@pytest.mark.parametrize("flags", [0, 4])   # 4: IGA_SOLVE_REFINE (FP32 corrections, FP64 residual)
+def test_adjoint_cg_start_and_refinement_change_only_rounding(flags):
     c = small_case()
     J0, g0 = gpu_adjoint(c, c["theta"], guess=0)
-    J3, g3 = gpu_adjoint(c, c["theta"], guess=3)
-    assert abs(J3 - J0) <= 1e-11 * J0
+    J3, g3 = gpu_adjoint(c, c["theta"], guess=3, flags=flags)
+    assert abs(J3 - J0) <= 1e-10 * J0
     assert np.abs(g3 - g0).max() <= 1e-9 * np.abs(g0).max()
 
 

@@ -378,7 +378,8 @@ def test_wave_fp32_error_against_fp64_oracle():
 
 
 @pytest.mark.parametrize("mode", ["f64", "f64_plain", "f64_graph", "f32", "f32_graph", "f64_guess2", "f32_guess2",
-                                  "f64_guess1", "f32_guess3", "f64_guess6", "f32_guess6", "f32_graph_guess4"])
+                                  "f64_guess1", "f32_guess3", "f64_guess6", "f32_guess6", "f32_graph_guess4",
+                                  "f64_refine", "f64_refine_guess3"])
 def test_wave_cube_ricker_source_matches_oracle(mode):
     """3-D, lognormal wave speed, Ricker point source at the centre (the bench workload family)."""
     name = "cube20_p2_theta_M2"
@@ -392,6 +393,8 @@ def test_wave_cube_ricker_source_matches_oracle(mode):
     f32 = mode.startswith("f32")
     dtype = iga.IGA_F32 if f32 else iga.IGA_F64
     flags = iga.IGA_SOLVE_PLAIN if "plain" in mode else iga.IGA_SOLVE_GRAPH if "graph" in mode else 0
+    if "refine" in mode:
+        flags |= iga.IGA_SOLVE_REFINE
     guess = int(mode[-1]) if "guess" in mode else 0
     wave = iga.iga_wave_create(ops, 1, dtype, dt, src_pos=src[None], f0=10.0, t0=0.1, rec_pos=rec,
                                nsteps_max=nsteps, cg_rtol=1e-6 if f32 else 1e-13,
