@@ -876,7 +876,63 @@ def oracle_sample(args):
                        "oracle leapfrog steps of the n_el=12 version (%.1f s; scaled by N); full pass "
                        "estimated at %.0f s" % (k, k, t_srows + t_rows, n_sample_rows, N, k,
                                                t_build_m + t_srow_m + t_true_m, steps_small, t_small, total)),
-            "surrogate_rows_per_s": N / asm_s, "sample_seconds": sample_s}
+            "surrogate_rows_per_s": N / asm_s, "sample_seconds": sample_s,
+            "_parts": {"N": N, "n_sample_rows": n_sample_rows, "interp_s": interp_s, "step_s": step_s,
+                       "nsteps": nsteps, "k": k}}
+
+
+def _oracle_rows_chunk(args):
+    """Surrogate.rows() of a chunk of rows (a process-pool task)."""
+    S, rows = args
+    return S.rows(rows)
+
+
+def oracle_sample_all_cores(args, single):
+    """The oracle's row-parallel parts on all host cores: true-row quadrature and surrogate
+    evaluation of `oracle_rows` x nproc random rows split over a process pool of nproc
+    workers (spawn start, the same per-row arithmetic), scaled to the full workload as in
+    the single-thread sample; the leapfrog part stays the single-thread measurement (one
+    shot, sparse products on one core).  Returns the cpu_baseline object of that run."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from oracle.surrogate import Surrogate, _true_rows_chunk
+    from paper_2004_05197_gb300 import workloads as W
+    from tests.oracle_cases import oracle_space
+    nproc = os.cpu_count() or 1
+    parts = single["_parts"]
+    w = W.scaled(args.workload)
+    sp = oracle_space(w)
+    rng = np.random.default_rng(1)
+    kk = parts["k"] * nproc
+    rows = sp.multi(rng.integers(0, sp.N, size=kk))
+    wm = W.scaled(args.workload, n_el=24)
+    spm = oracle_space(wm)
+    Sm = Surrogate(spm, wm["q"], wm["M"])
+    rows_m = spm.multi(rng.integers(0, spm.N, size=kk))
+    with cf.ProcessPoolExecutor(nproc, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_true_rows_chunk, [(sp, rows[:2])] * nproc))          # start-up of the workers
+        t = time.perf_counter()
+        list(ex.map(_true_rows_chunk, [(sp, c) for c in np.array_split(rows, nproc)]))
+        t_rows = time.perf_counter() - t
+        t = time.perf_counter()
+        list(ex.map(_oracle_rows_chunk, [(Sm, c) for c in np.array_split(rows_m, nproc)]))
+        t_srow = time.perf_counter() - t
+        t = time.perf_counter()
+        list(ex.map(_true_rows_chunk, [(spm, c) for c in np.array_split(rows_m, nproc)]))
+        t_true = time.perf_counter() - t
+    per_row = t_rows / kk
+    eval_s = max(t_srow - t_true, 0.0) / kk
+    N = parts["N"]
+    asm_s = (parts["n_sample_rows"] + N) * per_row + parts["interp_s"] + N * eval_s
+    total = asm_s + parts["nsteps"] * parts["step_s"]
+    return {"value": args.nshot * parts["nsteps"] / total, "unit": "shot-steps/s", "cores": nproc, "kind": "oracle",
+            "sample": ("the single-thread sample with its quadrature and evaluation parts re-run on %d cores "
+                       "(%d random rows each, process pool; %.1f s + %.1f s); the leapfrog part single-core; "
+                       "full pass estimated at %.0f s" % (nproc, kk, t_rows, t_srow + t_true, total)),
+            "surrogate_rows_per_s": N / asm_s}
 
 
 def workload_config(args, world=1):
@@ -942,6 +998,8 @@ def main():
     ap.add_argument("--oracle-rows", type=int, default=96)
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the oracle's row-parallel parts on all host cores")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-mesh leg")
     ap.add_argument("--batched-steps", type=int, default=1000)
@@ -994,7 +1052,11 @@ def main():
         if args.adjoint:
             out["components"].update(run_adjoint(args))
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = oracle_sample(args)
+            single = oracle_sample(args)
+            if args.cpu_all_cores:
+                out["cpu_baseline_all_cores"] = oracle_sample_all_cores(args, single)
+            single.pop("_parts", None)
+            out["cpu_baseline"] = single
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
