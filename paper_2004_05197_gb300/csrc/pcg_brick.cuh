@@ -1,14 +1,20 @@
 // Brick form of the persistent Jacobi-PCG (FP32 dtype, one right-hand side, 3-D
 // operators with a brick form).  Same recurrence, precision and stopping rule as
-// pcg_persistent_kernel (Chronopoulos-Gear form; FP64 residual, compensated FP32
-// dot products widened to FP64, fixed-order reductions), with the rows owned by
-// bricks instead of a grid-stride loop:
-//   * one CTA per brick for the whole solve (cooperative launch, one wave);
-//   * phase 1 updates the brick's own rows (p, s, x, r, u and the partials of
-//     (r,u), (r,r));
+// pcg_persistent_kernel (Chronopoulos-Gear form; compensated FP32 dot products
+// widened to FP64, fixed-order reductions), with the residual carried as a pair of
+// FP32 numbers instead of one FP64 number, and the rows owned by bricks instead
+// of a grid-stride loop:
+//   * one CTA per brick (and per SM) for the whole solve (cooperative launch, one
+//     wave); every compute lane owns one (x, y) column of its brick, the same in
+//     every phase;
+//   * the brick's own p, s, x, w = M~u, D^-1 and the residual pair live in the CTA's
+//     tensor memory (TMEM, tcgen05.alloc / ld / st) for the whole solve, and u of
+//     the brick's rows is still in the shared-memory tile of the last M~ pass, so
+//     the vector update reads nothing from global memory and writes only u (which
+//     the neighbouring bricks read); x is written back once at the end;
 //   * phase 2 loads the u tile of the brick grown by p (coherent loads: u was
 //     written by the neighbouring CTAs in phase 1), applies M~ with the brick
-//     kernels of brick.cuh, writes w and the partial of (w,u);
+//     kernels of brick.cuh and forms the partial of (w,u);
 //   * the phases are separated by a bounded grid barrier among the compute
 //     warps; the producer warp streams the M~ fields through the stage ring
 //     without waiting for the vectors (the fields are the same every pass), so
@@ -24,8 +30,11 @@ namespace iga {
 // counted by every CTA) is passed once it reaches e * nblocks, so an arrival is a
 // single atomic and nothing is reset in between.  The counter is zero at launch.
 // Bounded: on time-out bit 4 of *err is set and every caller leaves.
+// The error word is read once per CTA (by thread 0, into *verdict), so every
+// compute warp of the CTA takes the same branch afterwards.
 __device__ __forceinline__ bool compute_grid_barrier(unsigned* bar, int* err, unsigned nblocks, int ncw,
-                                                     long long spin_cycles, unsigned long long& epoch) {
+                                                     long long spin_cycles, unsigned long long& epoch,
+                                                     volatile int* verdict) {
     named_bar_sync(2, ncw * 32);
     epoch += 1;
     if (threadIdx.x == 0) {
@@ -46,9 +55,10 @@ __device__ __forceinline__ bool compute_grid_barrier(unsigned* bar, int* err, un
             }
         }
         __threadfence();
+        *verdict = *((volatile int*)err);
     }
     named_bar_sync(2, ncw * 32);
-    return *((volatile int*)err) == 0;
+    return *verdict == 0;
 }
 
 // Fixed-order block sum over the compute warps of K doubles per thread; the
@@ -127,10 +137,52 @@ __device__ __forceinline__ void stv(double* p, double v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
 }
 
+// ---- tensor memory of the CTA as storage for the brick's CG vectors.  With
+// the 32x32b shape, thread t of a warp accesses TMEM lane 32 * (warp % 4) + t,
+// one 32-bit column per .x1 access; the allocating warp writes the base address
+// into shared memory.  The loaded registers pass through the wait, so that no
+// use of them can be scheduled before it.
+constexpr unsigned kTmemCols = 512;   // the whole TMEM of the SM (one CTA per SM)
+constexpr int kTmemWords = 7;         // p, s, x, w, D^-1, r (high part), r (low part)
+__device__ __forceinline__ void tmem_alloc(unsigned* dst, unsigned ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ unsigned tmem_ld(unsigned taddr) {
+    unsigned v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void tmem_st(unsigned taddr, unsigned v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(unsigned& a, unsigned& b, unsigned& c, unsigned& d, unsigned& e,
+                                             unsigned& f, unsigned& g) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a), "+r"(b), "+r"(c), "+r"(d), "+r"(e), "+r"(f), "+r"(g)
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(unsigned& a) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a) : : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
 // Shared scratch of the brick PCG, placed in the first kBrickPcgHeader bytes of
 // the dynamic shared memory (the stage ring starts after it).
 struct BrickPcgShared {
     uint64_t full[4], empty[4];
+    unsigned tmem;         // TMEM base address (written by tcgen05.alloc)
+    int verdict;           // error word as read after the last grid barrier
     int done;              // set when the compute warps leave: the producer stops
     int active, iters;
     double gam, rr, bnorm, alpha, beta;
@@ -176,6 +228,56 @@ __device__ __forceinline__ void brick_produce_until_done(const BrickMaps& maps, 
     brick_drain<NS>(full, k);
 }
 
+// TMEM columns for a brick of nx x ny x nz rows: its warps (one per 4 x 8 lane
+// patch) that share a lane quarter take consecutive slots of kTmemWords * nz
+// columns (word k of plane zl at column slot + k * nz + zl); warps without rows
+// hold none.
+__host__ __device__ constexpr int brick_pcg_tmem_cols(int nx, int ny, int nz) {
+    return ((nx + 3) / 4 * ((ny + 7) / 8) + 3) / 4 * kTmemWords * nz;
+}
+
+// The residual of the brick PCG as an unevaluated pair hi + lo of FP32 numbers
+// (about 48 significant bits; the FP64 pipe of this part issues about 60 times
+// more slowly than the FP32 one).  ff_two_sum: Knuth's TwoSum, a + b = s + e
+// exactly.  ff_sub_prod: (hi, lo) -= (ahi + alo) s, with ahi s split exactly by
+// an FMA (Dekker / Kahan TwoProd), alo s rounded once, then renormalised.
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_sub_prod(float& hi, float& lo, float ahi, float alo, float s) {
+    const float p = __fmul_rn(ahi, s);
+    const float e = fmaf(ahi, s, -p);          // ahi s = p + e exactly
+    const float t = fmaf(alo, s, e);           // the part below p
+    float h, err;
+    ff_two_sum(hi, -p, h, err);
+    const float l = __fsub_rn(__fadd_rn(lo, err), t);
+    hi = __fadd_rn(h, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, h));
+}
+
+// End of an M~ pass: w = acc of the lane's rows into TMEM word 3; returns the
+// lane's partial of (w, u) (u = xo, the tile values of the same rows).
+template <int BZM>
+__device__ __forceinline__ double brick_pcg_keep_w(const float (&acc)[BZM], const float (&xo)[BZM],
+                                                   const BrickGeo& g, unsigned tw, int nzs) {
+    DotAcc<float> d0;
+#pragma unroll
+    for (int zl = 0; zl < BZM; ++zl) {
+        if (zl >= g.nz || !g.warp_ok) break;   // uniform over the warp
+        __syncwarp();
+        tmem_st(tw + (unsigned)(3 * nzs + zl), __float_as_uint(acc[zl]));
+        if (g.lane_ok) d0.add(xo[zl], acc[zl]);
+    }
+    tmem_wait_st();
+    return d0.value();
+}
+
+// Requirements checked by the host before the launch: one CTA per SM (the
+// launch asks for enough shared memory that a second CTA cannot fit, so the
+// allocation of the whole TMEM never waits) and brick_pcg_tmem_cols(nx, ny, nz)
+// <= kTmemCols for every brick.
 template <int P, int NS>
 __global__ void __launch_bounds__(1024, 1)
     pcg_brick_kernel(const __grid_constant__ BrickMaps maps, const BrickDesc* __restrict__ bricks, int nF,
@@ -194,9 +296,16 @@ __global__ void __launch_bounds__(1024, 1)
             mbar_init(&sh.empty[s], ncw);
         }
         sh.done = 0;
+        sh.verdict = 0;
         mbar_fence_init();
     }
+    if (warp == 0) {
+        tmem_alloc(&sh.tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
     const BrickDesc bd = bricks[blockIdx.x];
     if (warp == ncw) {
         if (lane == 0) {
@@ -209,11 +318,22 @@ __global__ void __launch_bounds__(1024, 1)
     const int m = v.m;
     const long long mm = (long long)m * m;
     const long long colbase = (long long)g.z0 * mm + (long long)(g.y0 + g.cy) * m + g.x0 + g.cx;
+    // this lane's TMEM words (lane quarter of the warp, column slot of its group)
+    const unsigned tw = sh.tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)((warp >> 2) * kTmemWords * g.nz);
+    const int nzs = g.nz;
+    auto tcol = [&](int k, int zl) { return tw + (unsigned)(k * nzs + zl); };
     unsigned long long fc = 0, epoch = 0;
     float acc[BZM], xo[BZM];
     double part[3];
     bool ok = true;
-    auto stop = [&]() {
+    // every compute warp of the CTA leaves through here, together (the barrier
+    // verdicts are CTA-uniform): TMEM is freed by the warp that allocated it
+    auto leave = [&]() {
+        tmem_wait_st();
+        tmem_fence_before();
+        named_bar_sync(1, ncw * 32);
+        tmem_fence_after();
+        if (warp == 0) tmem_dealloc(sh.tmem, kTmemCols);
         if (threadIdx.x == 0) {
             sh.done = 1;
             __threadfence_block();
@@ -221,56 +341,58 @@ __global__ void __launch_bounds__(1024, 1)
         cg_report(c);
     };
 
-    // ---- init 1: r = b - M~x, u = D^-1 r; partials (r,u), (r,r), (b,b)
+    // ---- init 1: r = b - M~x, u = D^-1 r; partials (r,u), (r,r), (b,b); TMEM
+    // gets p = s = 0, x, D^-1 and r of the lane's rows
     {
         brick_load_tile<P, true>(xt, v.x, g, m, warp, ncw, lane);
         ok = brick_pass<P, true, true, BZM, NS>(g, stages, stage_floats, xt, sh.full, sh.empty, fc, lane, acc, xo);
         fc += nF;
+        if (!ok) atomicOr(c.err, 16);
         DotAcc<float> d0, d1, d2;
-        if (g.lane_ok) {
 #pragma unroll
-            for (int zl = 0; zl < BZM; ++zl) {
-                if (zl >= g.nz) break;
-                const long long j = colbase + zl * mm;
-                const float bi = v.b[j];
-                const double ri = (double)bi - (double)acc[zl];   // FP64 residual
-                const float rt = (float)ri;
-                const float ui = v.dinv[j] * rt;
-                v.r[j] = ri;
+        for (int zl = 0; zl < BZM; ++zl) {
+            if (zl >= g.nz || !g.warp_ok) break;   // uniform over the warp
+            __syncwarp();
+            const long long j = colbase + zl * mm;
+            const float bi = g.lane_ok ? v.b[j] : 0.f;
+            const float di = g.lane_ok ? v.dinv[j] : 0.f;
+            float rhi, rlo;   // r = b - M~x exactly, as an unevaluated pair
+            ff_two_sum(bi, -acc[zl], rhi, rlo);
+            const float rt = rhi;
+            const float ui = di * rt;
+            tmem_st(tcol(0, zl), 0u);
+            tmem_st(tcol(1, zl), 0u);
+            tmem_st(tcol(2, zl), __float_as_uint(xo[zl]));
+            tmem_st(tcol(4, zl), __float_as_uint(di));
+            tmem_st(tcol(5, zl), __float_as_uint(rhi));
+            tmem_st(tcol(6, zl), __float_as_uint(rlo));
+            if (g.lane_ok) {
                 v.u[j] = ui;
                 d0.add(rt, ui);
                 d1.add(rt, rt);
                 d2.add(bi, bi);
             }
         }
+        tmem_wait_st();
         part[0] = d0.value();
         part[1] = d1.value();
         part[2] = d2.value();
         compute_block_sum<3>(part, sh.wsum, sh.red, ncw);
         if (threadIdx.x < 3) c.partials[(size_t)blockIdx.x * S + 6 + threadIdx.x] = sh.red[threadIdx.x];
     }
-    if (!ok) atomicOr(c.err, 16);
-    if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch)) return stop();
-    // ---- init 2: w = M~u; partial (w,u)
+    if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch, &sh.verdict)) return leave();
+    // ---- init 2: w = M~u into TMEM; partial (w,u)
     {
         brick_load_tile<P, true>(xt, v.u, g, m, warp, ncw, lane);
         ok = brick_pass<P, true, true, BZM, NS>(g, stages, stage_floats, xt, sh.full, sh.empty, fc, lane, acc, xo);
         fc += nF;
-        DotAcc<float> d0;
-        if (g.lane_ok) {
-#pragma unroll
-            for (int zl = 0; zl < BZM; ++zl) {
-                if (zl >= g.nz) break;
-                v.w[colbase + zl * mm] = acc[zl];
-                d0.add(xo[zl], acc[zl]);
-            }
-        }
-        part[0] = d0.value();
+        if (!ok) atomicOr(c.err, 16);
+        part[0] = brick_pcg_keep_w<BZM>(acc, xo, g, tw, nzs);
+
         compute_block_sum<1>(part, sh.wsum, sh.red, ncw);
         if (threadIdx.x == 0) c.partials[(size_t)blockIdx.x * S + 4] = sh.red[0];
     }
-    if (!ok) atomicOr(c.err, 16);
-    if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch)) return stop();
+    if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch, &sh.verdict)) return leave();
     compute_grid_sum<3>(c.partials, gridDim.x, S, 6, sh.red, ncw);
     compute_grid_sum<1>(c.partials, gridDim.x, S, 4, sh.red2, ncw);
     if (threadIdx.x == 0) {
@@ -289,72 +411,63 @@ __global__ void __launch_bounds__(1024, 1)
         sh.active = act;
     }
     named_bar_sync(1, ncw * 32);
-    // a zero right-hand side has the solution 0
-    if (!(sh.bnorm > 0.0) && g.lane_ok)
-        for (int zl = 0; zl < g.nz; ++zl) v.x[colbase + zl * mm] = 0.f;
 
     for (int it = 0; it < c.max_it && sh.active; ++it) {
         const int off1 = (it & 1) * 2;
-        // ---- phase 1 (own rows), x-runs of the brick for coalesced access
+        // ---- phase 1 (the lane's rows): p, s, x, w, D^-1, r from TMEM, u from the
+        // tile of the last M~ pass; only u goes to global memory
         {
             const float be = (float)sh.beta, al = (float)sh.alpha;
-            const double ald = sh.alpha;
+            const float ahi = (float)sh.alpha, alo = (float)(sh.alpha - (double)ahi);   // alpha as a pair
             const uint64_t pol = l2_evict_last_policy();
+            const int plane = g.byb * g.bxb, sb = (P * g.byb + g.cy + P) * g.bxb + g.cx + P;
             DotAcc<float> d0, d1;
-            const int nch = (g.nx + 31) / 32;   // 32-column chunks of an x-run
-            const int nitems = g.ny * g.nz * nch;
-            for (int item = warp; item < nitems; item += ncw) {
-                const int line = item / nch, xl = (item - line * nch) * 32 + lane;
-                if (xl >= g.nx) continue;
-                const int yl = line % g.ny, zl = line / g.ny;
-                const long long o = (long long)(g.z0 + zl) * mm + (long long)(g.y0 + yl) * m + g.x0 + xl;
-                const float di = ldv(v.dinv + o, pol);
-                const float pi = ldv(v.u + o, pol) + be * ldv(v.p + o, pol);
-                const float si = ldv(v.w + o, pol) + be * ldv(v.s + o, pol);
-                const float xi = ldv(v.x + o, pol);
-                const double rv = ldv(v.r + o, pol);
-                stv(v.p + o, pi, pol);
-                stv(v.s + o, si, pol);
-                stv(v.x + o, xi + al * pi, pol);
-                const double ri = rv - ald * (double)si;   // FP64 residual
-                const float rt = (float)ri;
-                const float ui = di * rt;
-                stv(v.r + o, ri, pol);
-                stv(v.u + o, ui, pol);
-                d0.add(rt, ui);
-                d1.add(rt, rt);
+#pragma unroll
+            for (int zl = 0; zl < BZM; ++zl) {
+                if (zl >= g.nz || !g.warp_ok) break;   // uniform over the warp
+                __syncwarp();
+                unsigned wp = tmem_ld(tcol(0, zl)), ws = tmem_ld(tcol(1, zl)), wx = tmem_ld(tcol(2, zl));
+                unsigned ww = tmem_ld(tcol(3, zl)), wd = tmem_ld(tcol(4, zl)), whi = tmem_ld(tcol(5, zl));
+                unsigned wlo = tmem_ld(tcol(6, zl));
+                const float uo = g.lane_ok ? xt[sb + zl * plane] : 0.f;
+                tmem_wait_ld(wp, ws, wx, ww, wd, whi, wlo);
+                const float pi = uo + be * __uint_as_float(wp);
+                const float si = __uint_as_float(ww) + be * __uint_as_float(ws);
+                const float xi = __uint_as_float(wx) + al * pi;
+                float rhi = __uint_as_float(whi), rlo = __uint_as_float(wlo);
+                ff_sub_prod(rhi, rlo, ahi, alo, si);   // r -= alpha s in pair arithmetic
+                const float rt = rhi;
+                const float ui = __uint_as_float(wd) * rt;
+                tmem_st(tcol(0, zl), __float_as_uint(pi));
+                tmem_st(tcol(1, zl), __float_as_uint(si));
+                tmem_st(tcol(2, zl), __float_as_uint(xi));
+                tmem_st(tcol(5, zl), __float_as_uint(rhi));
+                tmem_st(tcol(6, zl), __float_as_uint(rlo));
+                if (g.lane_ok) {
+                    stv(v.u + colbase + zl * mm, ui, pol);
+                    d0.add(rt, ui);
+                    d1.add(rt, rt);
+                }
             }
+            tmem_wait_st();
             part[0] = d0.value();
             part[1] = d1.value();
         }
         compute_block_sum<2>(part, sh.wsum, sh.red, ncw);
         if (threadIdx.x < 2) c.partials[(size_t)blockIdx.x * S + off1 + threadIdx.x] = sh.red[threadIdx.x];
-        if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch)) return stop();
-        // ---- phase 2: w = M~u; partial (w,u)
+        if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch, &sh.verdict)) return leave();
+        // ---- phase 2: w = M~u into TMEM; partial (w,u)
         {
             brick_load_tile<P, true>(xt, v.u, g, m, warp, ncw, lane);
             ok = brick_pass<P, true, true, BZM, NS>(g, stages, stage_floats, xt, sh.full, sh.empty, fc, lane, acc,
                                                     xo);
             fc += nF;
-            DotAcc<float> d0;
-            if (g.lane_ok) {
-                const uint64_t pol = l2_evict_last_policy();
-#pragma unroll
-                for (int zl = 0; zl < BZM; ++zl) {
-                    if (zl >= g.nz) break;
-                    stv(v.w + colbase + zl * mm, acc[zl], pol);
-                    d0.add(xo[zl], acc[zl]);
-                }
-            }
-            part[0] = d0.value();
+            if (!ok) atomicOr(c.err, 16);
+            part[0] = brick_pcg_keep_w<BZM>(acc, xo, g, tw, nzs);
             compute_block_sum<1>(part, sh.wsum, sh.red, ncw);
             if (threadIdx.x == 0) c.partials[(size_t)blockIdx.x * S + 4] = sh.red[0];
         }
-        if (!ok) {
-            atomicOr(c.err, 16);
-            return stop();
-        }
-        if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch)) return stop();
+        if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch, &sh.verdict)) return leave();
         compute_grid_sum3(c.partials, gridDim.x, S, off1, off1 + 1, 4, sh.red, ncw);
         if (threadIdx.x == 0) {
             int brk = 0, act = 1, iters = sh.iters;
@@ -370,7 +483,20 @@ __global__ void __launch_bounds__(1024, 1)
         }
         named_bar_sync(1, ncw * 32);
     }
-    stop();
+    // ---- x of the lane's rows back to global memory (a zero right-hand side has
+    // the solution 0)
+    {
+        const bool zero = !(sh.bnorm > 0.0);
+#pragma unroll
+        for (int zl = 0; zl < BZM; ++zl) {
+            if (zl >= g.nz || !g.warp_ok) break;   // uniform over the warp
+            __syncwarp();
+            unsigned wx = tmem_ld(tcol(2, zl));
+            tmem_wait_ld(wx);
+            if (g.lane_ok) v.x[colbase + zl * mm] = zero ? 0.f : __uint_as_float(wx);
+        }
+    }
+    leave();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rel = sh.bnorm > 0.0 ? sqrt(sh.rr) / sh.bnorm : 0.0;
         c.iters_out[0] = sh.iters;

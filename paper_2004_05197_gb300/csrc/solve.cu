@@ -696,8 +696,13 @@ static bool brick_pcg_launch(const iga_ops* ops, CgVecs<T>& v, CgCtl& c, cudaStr
     } else {
         if (!brick_usable(ops, IGA_OP_M)) return false;
         const BrickOps& bo = *ops->brick;
-        const size_t smem = kBrickPcgHeader + sizeof(float) * ((size_t)bo.ns * bo.stage_floats + bo.xt_floats);
+        // one CTA per SM: at least half the SM's shared memory, so that the
+        // kernel's allocation of the whole TMEM never waits for another CTA
+        const size_t smem = std::max<size_t>(
+            kBrickPcgHeader + sizeof(float) * ((size_t)bo.ns * bo.stage_floats + bo.xt_floats), 116 * 1024);
         if (smem > 227 * 1024) return false;
+        for (const BrickDesc& b : bo.host)
+            if (brick_pcg_tmem_cols(b.nx, b.ny, b.nz) > (int)kTmemCols) return false;
         const int threads = (bo.ncw + 1) * 32;
         auto fn3 = pcg_brick_kernel<P, 3>;
         auto fn2 = pcg_brick_kernel<P, 2>;
@@ -709,8 +714,8 @@ static bool brick_pcg_launch(const iga_ops* ops, CgVecs<T>& v, CgCtl& c, cudaStr
         int per = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1 ||
-            bo.nbricks > per * sms) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per != 1 ||
+            bo.nbricks > sms) {
             cudaGetLastError();
             return false;
         }
