@@ -330,6 +330,28 @@ static int encode_maps(BrickMaps& maps, const BrickOps& bo, void* base, int nF, 
     return IGA_OK;
 }
 
+// Tensor maps of the padded u copy: 3-D (XP, m, m), one box per class covering
+// the class's vector tile (the brick grown by P on every side).
+static int encode_tile_maps(BrickMaps& maps, const BrickOps& bo, void* base, const PlanResult& pr) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(IGA_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    std::memset(&maps, 0, sizeof(maps));
+    const cuuint64_t dims[3] = {(cuuint64_t)bo.XP, (cuuint64_t)bo.m, (cuuint64_t)bo.m};
+    const cuuint64_t strides[2] = {(cuuint64_t)bo.XP * 4, (cuuint64_t)bo.XP * bo.m * 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int c = 0; c < pr.ncls; ++c) {
+        const cuuint32_t box[3] = {(cuuint32_t)pr.bx[c], (cuuint32_t)pr.by[c], (cuuint32_t)(pr.bz[c] + bo.P)};
+        const CUresult r = enc(&maps.tm[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(IGA_ERR_CUDA, "cuTensorMapEncodeTiled failed for a vector tile box");
+        maps.bx[c] = pr.bx[c];
+        maps.by[c] = pr.by[c];
+        maps.bz[c] = pr.bz[c] + bo.P;
+    }
+    return IGA_OK;
+}
+
 int brick_prepare(iga_ops* ops, cudaStream_t st) {
     if (ops->dim != 3 || (ops->p != 1 && ops->p != 2) || !ops->fK32.ptr || !ops->fM32.ptr) return IGA_OK;
     const int P = ops->p, m = ops->m;
@@ -392,7 +414,10 @@ int brick_prepare(iga_ops* ops, cudaStream_t st) {
     }
     rc = encode_maps(bo->mapK, *bo, bo->fK.ptr, ops->nK, pr);
     if (!rc) rc = encode_maps(bo->mapM, *bo, bo->fM.ptr, ops->nM, pr);
+    if (!rc) rc = bo->upad.alloc(sizeof(float) * (size_t)bo->fsz);
+    if (!rc) rc = encode_tile_maps(bo->mapU, *bo, bo->upad.ptr, pr);
     if (rc) return rc;
+    IGA_CUDA(cudaMemsetAsync(bo->upad.ptr, 0, sizeof(float) * (size_t)bo->fsz, st));
     // dord is freed by its destructor: finish the copies that read it first
     IGA_CUDA(cudaStreamSynchronize(st));
     ops->brick = std::move(bo);

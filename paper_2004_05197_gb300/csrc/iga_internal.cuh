@@ -85,6 +85,10 @@ struct BrickOps {
     DevBuf fK, fM;                      // padded, group-ordered FP32 fields
     DevBuf err;                         // device error word of the brick kernels (bit 16: a wait timed out)
     BrickMaps mapK, mapM;
+    // padded copy of the PCG's u = D^-1 r ([m][m][XP], x offset P, zero padding) and
+    // its tensor maps (box = the class's vector tile: bx x by x (bz + P))
+    DevBuf upad;
+    BrickMaps mapU;
 };
 
 // On-the-fly evaluation of the stencil functions (onthefly.cu): per-line tables

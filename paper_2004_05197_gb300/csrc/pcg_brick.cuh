@@ -11,10 +11,11 @@
 //     tensor memory (TMEM, tcgen05.alloc / ld / st) for the whole solve, and u of
 //     the brick's rows is still in the shared-memory tile of the last M~ pass, so
 //     the vector update reads nothing from global memory and writes only u (which
-//     the neighbouring bricks read); x is written back once at the end;
-//   * phase 2 loads the u tile of the brick grown by p (coherent loads: u was
-//     written by the neighbouring CTAs in phase 1), applies M~ with the brick
-//     kernels of brick.cuh and forms the partial of (w,u);
+//     the neighbouring bricks read) into a padded copy; x is written back once at
+//     the end;
+//   * phase 2 loads the u tile of the brick grown by p from the padded copy as one
+//     TMA box (u was written by the neighbouring CTAs in phase 1), applies M~ with
+//     the brick kernels of brick.cuh and forms the partial of (w,u);
 //   * the phases are separated by a bounded grid barrier among the compute
 //     warps; the producer warp streams the M~ fields through the stage ring
 //     without waiting for the vectors (the fields are the same every pass), so
@@ -181,6 +182,7 @@ __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence
 // the dynamic shared memory (the stage ring starts after it).
 struct BrickPcgShared {
     uint64_t full[4], empty[4];
+    uint64_t tile_full;    // the u tile's TMA box has landed
     unsigned tmem;         // TMEM base address (written by tcgen05.alloc)
     int verdict;           // error word as read after the last grid barrier
     int done;              // set when the compute warps leave: the producer stops
@@ -280,8 +282,9 @@ __device__ __forceinline__ double brick_pcg_keep_w(const float (&acc)[BZM], cons
 // <= kTmemCols for every brick.
 template <int P, int NS>
 __global__ void __launch_bounds__(1024, 1)
-    pcg_brick_kernel(const __grid_constant__ BrickMaps maps, const BrickDesc* __restrict__ bricks, int nF,
-                     int stage_floats, CgVecs<float> v, CgCtl c) {
+    pcg_brick_kernel(const __grid_constant__ BrickMaps maps, const __grid_constant__ BrickMaps umaps,
+                     const BrickDesc* __restrict__ bricks, int nF, int stage_floats, float* __restrict__ upad, int XP,
+                     CgVecs<float> v, CgCtl c) {
     constexpr int BZM = 12;
     constexpr int S = kCgStride<1>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -295,6 +298,7 @@ __global__ void __launch_bounds__(1024, 1)
             mbar_init(&sh.full[s], 1);
             mbar_init(&sh.empty[s], ncw);
         }
+        mbar_init(&sh.tile_full, 1);
         sh.done = 0;
         sh.verdict = 0;
         mbar_fence_init();
@@ -341,6 +345,23 @@ __global__ void __launch_bounds__(1024, 1)
         cg_report(c);
     };
 
+    // u of the lane's row zl in the padded copy
+    float* const ucol = upad + ((long long)g.z0 * m + g.y0 + g.cy) * XP + g.x0 + g.cx + P;
+    const long long uplane = (long long)m * XP;
+    // u tile of the brick grown by P (zero outside the grid) as one TMA box.  Called
+    // right after a grid barrier: every read of xt in this CTA and every u store of
+    // the grid are done; the proxy fence orders them before the async-proxy copy.
+    unsigned tile_par = 0;
+    auto load_u_tile = [&]() {
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&sh.tile_full, (unsigned)(umaps.bx[g.cls] * umaps.by[g.cls] * umaps.bz[g.cls]) * 4u);
+            tma_load_3d(xt, &umaps.tm[g.cls], g.x0, g.y0 - P, g.z0 - P, &sh.tile_full);
+        }
+        if (!mbar_wait(&sh.tile_full, tile_par, kBrickWaitNs)) atomicOr(c.err, 16);
+        tile_par ^= 1u;
+    };
+
     // ---- init 1: r = b - M~x, u = D^-1 r; partials (r,u), (r,r), (b,b); TMEM
     // gets p = s = 0, x, D^-1 and r of the lane's rows
     {
@@ -367,7 +388,7 @@ __global__ void __launch_bounds__(1024, 1)
             tmem_st(tcol(5, zl), __float_as_uint(rhi));
             tmem_st(tcol(6, zl), __float_as_uint(rlo));
             if (g.lane_ok) {
-                v.u[j] = ui;
+                ucol[zl * uplane] = ui;
                 d0.add(rt, ui);
                 d1.add(rt, rt);
                 d2.add(bi, bi);
@@ -383,7 +404,7 @@ __global__ void __launch_bounds__(1024, 1)
     if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch, &sh.verdict)) return leave();
     // ---- init 2: w = M~u into TMEM; partial (w,u)
     {
-        brick_load_tile<P, true>(xt, v.u, g, m, warp, ncw, lane);
+        load_u_tile();
         ok = brick_pass<P, true, true, BZM, NS>(g, stages, stage_floats, xt, sh.full, sh.empty, fc, lane, acc, xo);
         fc += nF;
         if (!ok) atomicOr(c.err, 16);
@@ -444,7 +465,7 @@ __global__ void __launch_bounds__(1024, 1)
                 tmem_st(tcol(5, zl), __float_as_uint(rhi));
                 tmem_st(tcol(6, zl), __float_as_uint(rlo));
                 if (g.lane_ok) {
-                    stv(v.u + colbase + zl * mm, ui, pol);
+                    stv(ucol + zl * uplane, ui, pol);
                     d0.add(rt, ui);
                     d1.add(rt, rt);
                 }
@@ -458,7 +479,7 @@ __global__ void __launch_bounds__(1024, 1)
         if (!compute_grid_barrier(c.bar, c.err, gridDim.x, ncw, c.spin_cycles, epoch, &sh.verdict)) return leave();
         // ---- phase 2: w = M~u into TMEM; partial (w,u)
         {
-            brick_load_tile<P, true>(xt, v.u, g, m, warp, ncw, lane);
+            load_u_tile();
             ok = brick_pass<P, true, true, BZM, NS>(g, stages, stage_floats, xt, sh.full, sh.empty, fc, lane, acc,
                                                     xo);
             fc += nF;

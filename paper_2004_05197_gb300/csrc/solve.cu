@@ -720,9 +720,11 @@ static bool brick_pcg_launch(const iga_ops* ops, CgVecs<T>& v, CgCtl& c, cudaStr
             return false;
         }
         const BrickMaps* maps = &bo.mapM;
+        const BrickMaps* umaps = &bo.mapU;
         const BrickDesc* bricks = bo.bricks.as<BrickDesc>();
-        int nF = ops->nM, sf = bo.stage_floats;
-        void* args[] = {(void*)maps, (void*)&bricks, &nF, &sf, &v, &c};
+        int nF = ops->nM, sf = bo.stage_floats, XP = bo.XP;
+        float* upad = bo.upad.as<float>();
+        void* args[] = {(void*)maps, (void*)umaps, (void*)&bricks, &nF, &sf, &upad, &XP, &v, &c};
         const cudaError_t e = cudaLaunchCooperativeKernel(fn, bo.nbricks, threads, args, smem, st);
         count_launch();
         if (e != cudaSuccess) {
