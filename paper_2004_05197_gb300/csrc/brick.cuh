@@ -171,45 +171,37 @@ __device__ __forceinline__ BrickGeo brick_geo(const BrickMaps& maps, const Brick
 
 // Vector tile of the brick grown by P on every side ([z][y][x], row pitch bxb,
 // plane byb * bxb), zero outside the grid.  Called by the consumer warps only;
-// ends with their named barrier.  Each warp loads eight tile rows (two values per
-// lane and row) before it stores any, so a tile costs about two L2 round trips
-// instead of one per row.  COHERENT: plain loads (vectors written earlier in the
-// same persistent launch), else read-only loads.
-template <int P, bool COHERENT>
+// ends with their named barrier.  Each warp loads U tile rows of a 32-column
+// chunk (one value per lane and row) before it stores any, so a tile costs about
+// rows / (U * ncw) L2 round trips per chunk.  COHERENT: plain loads (vectors
+// written earlier in the same persistent launch), else read-only loads.
+template <int P, bool COHERENT, int U = 8>
 __device__ __forceinline__ void brick_load_tile(float* xt, const float* x, const BrickGeo& g, int m, int cwarp,
                                                 int ncw, int lane) {
-    constexpr int U = 8;
     const int zt = g.nz + 2 * P, rows = g.byb * zt;
     const long long mm = (long long)m * m;
-    for (int xc = 0; xc < g.bxb; xc += 64)   // one pass for boxes up to 64 columns
+    for (int xc = 0; xc < g.bxb; xc += 32)
     for (int r0 = cwarp; r0 < rows; r0 += U * ncw) {
-        const int ia = xc + lane, ib = ia + 32;
-        const int xa = g.x0 - P + ia, xb = xa + 32;
+        const int ia = xc + lane;
+        const int xa = g.x0 - P + ia;
         const bool oka = ia < g.bxb && xa >= 0 && xa < m;
-        const bool okb = ib < g.bxb && xb >= 0 && xb < m;
-        float va[U], vb[U];
+        float va[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int r = r0 + u * ncw;
             va[u] = 0.f;
-            vb[u] = 0.f;
             if (r < rows) {
                 const int yy = g.y0 - P + r % g.byb, zz = g.z0 - P + r / g.byb;
-                if (yy >= 0 && yy < m && zz >= 0 && zz < m) {
-                    const float* src = x + zz * mm + (long long)yy * m;
-                    if (oka) va[u] = COHERENT ? src[xa] : __ldg(src + xa);
-                    if (okb) vb[u] = COHERENT ? src[xb] : __ldg(src + xb);
+                if (oka && yy >= 0 && yy < m && zz >= 0 && zz < m) {
+                    const float* src = x + zz * mm + (long long)yy * m + xa;
+                    va[u] = COHERENT ? *src : __ldg(src);
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int r = r0 + u * ncw;
-            if (r < rows) {
-                float* dst = xt + (size_t)r * g.bxb;
-                if (ia < g.bxb) dst[ia] = va[u];
-                if (ib < g.bxb) dst[ib] = vb[u];
-            }
+            if (r < rows && ia < g.bxb) xt[(size_t)r * g.bxb + ia] = va[u];
         }
     }
     named_bar_sync(1, ncw * 32);
