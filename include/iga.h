@@ -64,6 +64,9 @@ extern "C" {
 #define IGA_MAP_ANNULUS_SECTOR   3  /* F(s,t) = (r cos a, r sin a), r = r0 + (r1-r0) s,
                                        a = a0 + (a1-a0) t, (r0, r1, a0, a1) = sector[]: one patch of
                                        a multi-patch annulus; det J = (r1-r0)(a1-a0) r must be > 0 */
+#define IGA_MAP_BOX              4  /* x_k = o_k + e_k s_k, (o_1..o_3, e_1..e_3) = box[]: an
+                                       axis-aligned box, one patch of a multi-patch brick; a
+                                       negative e_k runs s_k against x_k; det J = prod e_k > 0 */
 
 #define IGA_COEF_CONST    0  /* c = coef_param */
 #define IGA_COEF_SINCOS   1  /* c(x) = 1 + coef_param sin(2 pi x_1) cos(2 pi x_2), x = F(s) physical */
@@ -128,6 +131,7 @@ typedef struct iga_space_desc {
     int theta_degree;      /* BSPLINE: degree of the coefficient spline, 1..5 */
     int quad_pts;          /* Gauss points per direction and element; 0 => p+1 (Sec. 5.1); <= 8 */
     double sector[4];      /* ANNULUS_SECTOR: r0, r1, a0, a1 (radians) */
+    double box[6];         /* BOX: o_1, o_2, o_3, e_1, e_2, e_3 (2-D uses the first two of each) */
 } iga_space_desc;
 
 typedef struct iga_space_info {
@@ -447,24 +451,27 @@ int iga_wave_adjoint(iga_wave* wave, int nsteps, int checkpoint_every, const dou
 
 /* ---- multi-patch ---------------------------------------------------------
  * Sec. 3.2 and Sec. 3.4 (remarks on multi-patch geometries): a domain split into
- * 2-D patches, each with its own map, coefficient and surrogate fields (one
- * iga_ops per patch, assembled on its own space), glued along whole sides into
- * the C0-conforming multi-patch space.  The global matrix is the sum over
+ * 2-D or 3-D patches, each with its own map, coefficient and surrogate fields
+ * (one iga_ops per patch, assembled on its own space), glued along whole sides
+ * (2-D) or faces (3-D) into the C0-conforming multi-patch space.  The global matrix is the sum over
  * patches of P_l^T A_l P_l.  Global numbering: the local functions are visited
  * patch by patch, each patch in colex order, and every class of functions
  * identified by the interfaces takes the next global index at its first member.
  */
 typedef struct iga_multipatch iga_multipatch;
 typedef struct iga_interface {
-    int patch_a, side_a;   /* side: 0 = {i_1 = 0}, 1 = {i_1 = m-1}, 2 = {i_2 = 0}, 3 = {i_2 = m-1} */
+    int patch_a, side_a;   /* side 2k = {i_(k+1) = 0}, side 2k+1 = {i_(k+1) = m-1}: 0..3 in 2-D,
+                              0..5 in 3-D; its entries run colex over the remaining indices */
     int patch_b, side_b;   /* the two sides must have the same number m of functions */
-    int reversed;          /* 0: entry k meets entry k; 1: entry k meets entry m-1-k
-                              (entries ordered by the other index along the side) */
+    int reversed;          /* orientation.  2-D: 0 = entry k meets entry k, 1 = entry m-1-k.
+                              3-D (entry (u, v) of side a, u the faster index): bit 2 swaps u
+                              and v, then bit 0 reverses u (u -> m-1-u) and bit 1 reverses v;
+                              the result is the entry of side b that meets it */
 } iga_interface;
 
-/* patches: npatch borrowed iga_ops (2-D, same p; they must outlive the handle).
- * Builds the numbering and the inverse Jacobi diagonal of the global M~.
- * Errors: IGA_ERR_ARG (bad interface, unequal sides, 3-D patch),
+/* patches: npatch borrowed iga_ops (same dimension and p; they must outlive the
+ * handle).  Builds the numbering and the inverse Jacobi diagonal of the global M~.
+ * Errors: IGA_ERR_ARG (bad interface or orientation, unequal sides, mixed dimensions),
  * IGA_ERR_NONFINITE (non-positive global mass diagonal).  Synchronous. */
 int iga_multipatch_create(int npatch, const iga_ops* const* patches, int ninterface,
                           const iga_interface* interfaces, iga_multipatch** out);

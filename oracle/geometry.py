@@ -64,6 +64,25 @@ class AnnulusSector:
         return x, J
 
 
+class BoxMap:
+    """x_k = o_k + e_k s_k: an axis-aligned box, one patch of a multi-patch brick (the
+    multi-patch remark of Sec. 3.2 in three dimensions); J = diag(e).  A negative e_k
+    runs the parametric direction against the physical one (det J = prod e_k > 0)."""
+
+    def __init__(self, origin, extent):
+        self.origin = np.asarray(origin, dtype=np.float64)
+        self.extent = np.asarray(extent, dtype=np.float64)
+        self.dim = len(self.origin)
+
+    def __call__(self, s):
+        s = np.asarray(s, dtype=np.float64)
+        x = self.origin + self.extent * s
+        J = np.zeros(s.shape + (self.dim,))
+        for k in range(self.dim):
+            J[..., k, k] = self.extent[k]
+        return x, J
+
+
 class CubeSinePerturbed:
     """x_k = s_k + eps * sin(pi s) sin(pi t) sin(pi u) for each coordinate k (unit cube)."""
     dim = 3

@@ -12,9 +12,12 @@ patches are visited patch by patch, each patch in colexicographic order; the
 functions glued by the interfaces form equivalence classes, and a class receives
 the next global index when its first member is visited.
 
-Sides of a 2-D patch: 0 = {i_1 = 0}, 1 = {i_1 = m-1}, 2 = {i_2 = 0}, 3 = {i_2 = m-1};
-the functions along a side are ordered by the other index, and a reversed
-interface pairs entry k of one side with entry m-1-k of the other.
+Sides of a patch: side 2k is {i_(k+1) = 0} and side 2k+1 is {i_(k+1) = m-1}, so 2-D
+patches have sides 0..3 (m functions each) and 3-D patches faces 0..5 (m^2 functions each).
+The functions on a side are ordered colexicographically by the remaining indices.  The
+orientation code of an interface says which entry of side b meets entry (u, v) of side a
+(u the faster index): bit 2 swaps u and v, then bit 0 reverses u and bit 1 reverses v.  In
+2-D only bit 0 exists (the reversed flag).
 """
 import numpy as np
 import scipy.sparse as sps
@@ -22,26 +25,47 @@ import scipy.sparse as sps
 from .assembly import stencil_to_csr
 
 
-def side_indices(m, side):
-    """Linear (colex) local indices of the m functions on one side of a 2-D patch."""
-    k = np.arange(m)
-    if side == 0:
-        return k * m
-    if side == 1:
-        return k * m + (m - 1)
-    if side == 2:
-        return k
-    if side == 3:
-        return (m - 1) * m + k
-    raise ValueError("side must be 0..3")
+def side_indices(m, side, dim=2):
+    """Linear (colex) local indices of the functions on one side of a patch with m
+    functions per direction, ordered colex by the remaining indices."""
+    axis, top = divmod(side, 2)
+    if not (0 <= axis < dim):
+        raise ValueError("side must be 0..%d" % (2 * dim - 1))
+    f = np.arange(m ** (dim - 1))
+    coords = [f % m, f // m]             # the remaining indices, the first one fastest
+    idx = [None] * dim
+    idx[axis] = np.full(f.shape, m - 1 if top else 0)
+    for r, k in enumerate([k for k in range(dim) if k != axis]):
+        idx[k] = coords[r]
+    return sum(idx[k] * m ** k for k in range(dim))
 
 
-def global_numbering(ms, interfaces):
+def oriented(m, dim, orient):
+    """Position, in side b's order, of the partner of each entry of side a."""
+    if dim == 2:
+        if orient not in (0, 1):
+            raise ValueError("2-D interfaces take orient 0 or 1")
+        k = np.arange(m)
+        return m - 1 - k if orient else k
+    if not (0 <= orient < 8):
+        raise ValueError("3-D interfaces take orient 0..7")
+    v, u = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    u, v = u.ravel(), v.ravel()          # entry u + m v of side a
+    if orient & 4:
+        u, v = v, u
+    if orient & 1:
+        u = m - 1 - u
+    if orient & 2:
+        v = m - 1 - v
+    return u + m * v
+
+
+def global_numbering(ms, interfaces, dim=2):
     """Local-to-global maps (list of arrays, one per patch) and the global size.
 
     ms: functions per direction of each patch; interfaces: (patch_a, side_a,
-    patch_b, side_b, reversed) tuples, the glued sides having the same m."""
-    offs = np.concatenate([[0], np.cumsum([m * m for m in ms])])
+    patch_b, side_b, orient) tuples, the glued sides having the same m."""
+    offs = np.concatenate([[0], np.cumsum([m ** dim for m in ms])])
     parent = np.arange(offs[-1])
 
     def find(a):
@@ -50,13 +74,12 @@ def global_numbering(ms, interfaces):
             a = parent[a]
         return a
 
-    for pa, sa, pb, sb, rev in interfaces:
+    for pa, sa, pb, sb, orient in interfaces:
         if ms[pa] != ms[pb]:
             raise ValueError("glued sides need the same number of functions")
-        ia = offs[pa] + side_indices(ms[pa], sa)
-        ib = offs[pb] + side_indices(ms[pb], sb)
-        if rev:
-            ib = ib[::-1]
+        m = ms[pa]
+        ia = offs[pa] + side_indices(m, sa, dim)
+        ib = (offs[pb] + side_indices(m, sb, dim))[oriented(m, dim, orient)]
         for a, b in zip(ia, ib):
             ra, rb = find(a), find(b)
             if ra != rb:

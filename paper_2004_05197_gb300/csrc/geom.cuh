@@ -45,6 +45,11 @@ __device__ inline void map_eval(const GeomParams& gp, const double* s, double* x
         J[0][1] = -r * da * sn;
         J[1][0] = dr * sn;
         J[1][1] = r * da * cs;
+    } else if (gp.map_kind == IGA_MAP_BOX) {
+        for (int k = 0; k < d; ++k) {
+            x[k] = gp.box[k] + gp.box[3 + k] * s[k];
+            J[k][k] = gp.box[3 + k];
+        }
     } else if (gp.map_kind == IGA_MAP_CUBE_SINE) {
         double sn[3], cs[3];
         for (int k = 0; k < 3; ++k) sincospi(s[k], &sn[k], &cs[k]);

@@ -43,6 +43,7 @@ struct GeomParams {
     int map_kind;
     double map_param;
     double sector[4];      // ANNULUS_SECTOR: r0, r1, a0, a1
+    double box[6];         // BOX: origin (3), extent (3)
     int coef_kind;
     double coef_param;
     const double* theta;   // [n_theta^dim] colex

@@ -11,8 +11,9 @@
 // host-driven (two scalar read-backs per iteration): the plain schedule.
 //
 // Global numbering: local functions visited patch by patch, each patch in
-// colexicographic order; the side functions identified by the interfaces form
-// classes, and a class takes the next global index at its first member.
+// colexicographic order; the side functions identified by the interfaces (sides
+// of 2-D patches, faces of 3-D patches) form classes, and a class takes the next
+// global index at its first member.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -36,13 +37,26 @@ struct iga_multipatch {
 namespace iga {
 namespace {
 
-long long side_index(int m, int side, int k) {
-    switch (side) {
-        case 0: return (long long)k * m;
-        case 1: return (long long)k * m + (m - 1);
-        case 2: return k;
-        default: return (long long)(m - 1) * m + k;
-    }
+// Linear (colex) local index of entry e of a side: side 2k is {i_(k+1) = 0}, side
+// 2k+1 is {i_(k+1) = m-1}; the entries run colex over the remaining indices.
+long long side_index(int dim, int m, int side, long long e) {
+    const int axis = side / 2;
+    const long long c[2] = {e % m, e / m};   // remaining indices, the first one fastest
+    long long idx = 0, stride = 1;
+    int r = 0;
+    for (int k = 0; k < dim; ++k, stride *= m) idx += stride * (k == axis ? (side % 2 ? m - 1 : 0) : c[r++]);
+    return idx;
+}
+
+// Entry of side b that meets entry e = u + m v of side a: bit 2 of orient swaps u
+// and v, then bit 0 reverses u and bit 1 reverses v (2-D: e = u, bit 0 only).
+long long oriented_entry(int dim, int m, int orient, long long e) {
+    if (dim == 2) return (orient & 1) ? m - 1 - e : e;
+    long long u = e % m, v = e / m;
+    if (orient & 4) std::swap(u, v);
+    if (orient & 1) u = m - 1 - u;
+    if (orient & 2) v = m - 1 - v;
+    return u + (long long)m * v;
 }
 
 long long uf_find(std::vector<long long>& parent, long long a) {
@@ -209,7 +223,7 @@ extern "C" int iga_multipatch_create(int npatch, const iga_ops* const* patches, 
     *out = nullptr;
     for (int l = 0; l < npatch; ++l) {
         if (!patches[l]) return fail(IGA_ERR_ARG, "null patch");
-        if (patches[l]->dim != 2) return fail(IGA_ERR_ARG, "multi-patch gluing is implemented for 2-D patches");
+        if (patches[l]->dim != patches[0]->dim) return fail(IGA_ERR_ARG, "patches must share the dimension");
         if (patches[l]->p != patches[0]->p) return fail(IGA_ERR_ARG, "patches must share the degree p");
     }
     iga_multipatch* mp = new (std::nothrow) iga_multipatch();
@@ -234,16 +248,21 @@ extern "C" int iga_multipatch_create(int npatch, const iga_ops* const* patches, 
     std::iota(parent.begin(), parent.end(), 0LL);
     for (int f = 0; f < ninterface; ++f) {
         const iga_interface& it = ifs[f];
+        const int dim = patches[0]->dim;
         if (it.patch_a < 0 || it.patch_a >= npatch || it.patch_b < 0 || it.patch_b >= npatch ||
-            it.side_a < 0 || it.side_a > 3 || it.side_b < 0 || it.side_b > 3)
+            it.side_a < 0 || it.side_a >= 2 * dim || it.side_b < 0 || it.side_b >= 2 * dim)
             return bail(fail(IGA_ERR_ARG, "interface names a patch or side that does not exist"));
+        if (it.reversed < 0 || it.reversed > (dim == 2 ? 1 : 7))
+            return bail(fail(IGA_ERR_ARG, "orientation must be 0..1 (2-D) or 0..7 (3-D)"));
         const int ma = patches[it.patch_a]->m, mb = patches[it.patch_b]->m;
         if (ma != mb) return bail(fail(IGA_ERR_ARG, "glued sides need the same number of functions"));
         if (it.patch_a == it.patch_b && it.side_a == it.side_b)
             return bail(fail(IGA_ERR_ARG, "a side cannot be glued to itself"));
-        for (int k = 0; k < ma; ++k) {
-            const long long a = mp->off[it.patch_a] + side_index(ma, it.side_a, k);
-            const long long b = mp->off[it.patch_b] + side_index(mb, it.side_b, it.reversed ? ma - 1 - k : k);
+        const long long ne = dim == 2 ? ma : (long long)ma * ma;
+        for (long long k = 0; k < ne; ++k) {
+            const long long a = mp->off[it.patch_a] + side_index(dim, ma, it.side_a, k);
+            const long long b =
+                mp->off[it.patch_b] + side_index(dim, mb, it.side_b, oriented_entry(dim, ma, it.reversed, k));
             const long long ra = uf_find(parent, a), rb = uf_find(parent, b);
             if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
         }

@@ -79,7 +79,12 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
     if (d.map_kind == IGA_MAP_ANNULUS_QUARTER && d.dim != 2)
         return fail(IGA_ERR_ARG, "ANNULUS_QUARTER map is 2-D");
     if (d.map_kind == IGA_MAP_CUBE_SINE && d.dim != 3) return fail(IGA_ERR_ARG, "CUBE_SINE map is 3-D");
-    if (d.map_kind < 0 || d.map_kind > 3) return fail(IGA_ERR_ARG, "unknown map_kind");
+    if (d.map_kind < 0 || d.map_kind > 4) return fail(IGA_ERR_ARG, "unknown map_kind");
+    if (d.map_kind == IGA_MAP_BOX) {
+        double det = 1.0;
+        for (int k = 0; k < d.dim; ++k) det *= d.box[3 + k];
+        if (!(det > 0.0)) return fail(IGA_ERR_ARG, "BOX map needs a positive extent product (det J > 0)");
+    }
     if (d.map_kind == IGA_MAP_ANNULUS_SECTOR) {
         if (d.dim != 2) return fail(IGA_ERR_ARG, "ANNULUS_SECTOR map is 2-D");
         const double dr = d.sector[1] - d.sector[0], da = d.sector[3] - d.sector[2];
@@ -173,6 +178,7 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
     gp.map_kind = d.map_kind;
     gp.map_param = d.map_param;
     for (int k = 0; k < 4; ++k) gp.sector[k] = d.sector[k];
+    for (int k = 0; k < 6; ++k) gp.box[k] = d.box[k];
     gp.coef_kind = d.coef_kind;
     gp.coef_param = d.coef_param;
     gp.theta = s->theta.as<double>();

@@ -22,7 +22,7 @@ _lib = C.CDLL(LIB_PATH)
 IGA_OK = 0
 IGA_ERR_ARG, IGA_ERR_OOM, IGA_ERR_CUDA = -1, -2, -3
 IGA_ERR_NOT_CONVERGED, IGA_ERR_NONFINITE, IGA_ERR_TIMEOUT = -4, -5, -6
-IGA_MAP_IDENTITY, IGA_MAP_ANNULUS_QUARTER, IGA_MAP_CUBE_SINE, IGA_MAP_ANNULUS_SECTOR = 0, 1, 2, 3
+IGA_MAP_IDENTITY, IGA_MAP_ANNULUS_QUARTER, IGA_MAP_CUBE_SINE, IGA_MAP_ANNULUS_SECTOR, IGA_MAP_BOX = 0, 1, 2, 3, 4
 IGA_COEF_CONST, IGA_COEF_SINCOS, IGA_COEF_BSPLINE = 0, 1, 2
 IGA_F32, IGA_F64 = 0, 1
 IGA_OP_K, IGA_OP_M = 0, 1
@@ -56,7 +56,7 @@ class iga_space_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("n_el", C.c_int), ("map_kind", C.c_int),
                 ("map_param", C.c_double), ("coef_kind", C.c_int), ("coef_param", C.c_double),
                 ("theta", C.POINTER(C.c_double)), ("n_theta", C.c_int), ("theta_degree", C.c_int),
-                ("quad_pts", C.c_int), ("sector", C.c_double * 4)]
+                ("quad_pts", C.c_int), ("sector", C.c_double * 4), ("box", C.c_double * 6)]
 
 
 class iga_space_info(C.Structure):
@@ -180,15 +180,17 @@ def _host_f64(a):
 
 # ---- space ---------------------------------------------------------------------
 def iga_space_create(dim, p, n_el, map_kind, map_param=0.0, coef_kind=IGA_COEF_CONST, coef_param=1.0,
-                     theta=None, n_theta=0, theta_degree=3, quad_pts=0, sector=(0.0, 0.0, 0.0, 0.0)):
+                     theta=None, n_theta=0, theta_degree=3, quad_pts=0, sector=(0.0, 0.0, 0.0, 0.0),
+                     box=(0.0, 0.0, 0.0, 1.0, 1.0, 1.0)):
     """theta: host array, colex flat (first parametric direction fastest);
-    sector: (r0, r1, a0, a1) of IGA_MAP_ANNULUS_SECTOR."""
+    sector: (r0, r1, a0, a1) of IGA_MAP_ANNULUS_SECTOR; box: (o1, o2, o3, e1, e2, e3) of
+    IGA_MAP_BOX."""
     keep = None
     tptr = C.POINTER(C.c_double)()
     if theta is not None:
         keep, tptr = _host_f64(np.asarray(theta).ravel())
     desc = iga_space_desc(dim, p, n_el, map_kind, map_param, coef_kind, coef_param, tptr, n_theta,
-                          theta_degree, quad_pts, (C.c_double * 4)(*sector))
+                          theta_degree, quad_pts, (C.c_double * 4)(*sector), (C.c_double * 6)(*box))
     out = C.c_void_p()
     _check(_lib.iga_space_create(C.byref(desc), C.byref(out)))
     del keep
