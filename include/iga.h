@@ -494,6 +494,29 @@ int iga_multipatch_mass_solve(const iga_multipatch* mp, int dtype, const void* b
                               double rtol, int max_it, int* iters_out, double* relres_out,
                               void* stream);
 
+/* Leapfrog on the multi-patch surrogate operators: the scheme of iga_wave_step
+ * (Sec. 4.6 time stepping with surrogate matrices; the scheme itself is this
+ * library's, the paper has none) on the glued space:
+ *   u^{n+1} = 2 u^n - u^{n-1} + dt^2 a^n,  M~ a^n = f^n - K~ u^n,
+ *   u^1 = u^0 + dt^2/2 a^0 (zero initial velocity),
+ * a^n by the multi-patch Jacobi-PCG (rtol cg_rtol, at most cg_max_it iterations per
+ * step) started from a^{n-1} (0 at n = 0), f^n = amp r(n dt) B(s_src) with the Ricker
+ * wavelet r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2) and B(s_src)
+ * the global basis at parametric point src_s of patch src_patch (src_patch < 0: no
+ * source), and receiver traces d_r^n = sum_i u_i^n B_i(rec_s[r]) in patch
+ * rec_patch[r] for n = 1..nsteps.  FP32 carries the state as an unevaluated pair
+ * of FP32 numbers (the applies read the high part).
+ *   u       device [n_global] of dtype: u^0 in, u^nsteps out
+ *   src_s   host [dim] parametric point; rec_patch host [nrec]; rec_s host [nrec][dim]
+ *   traces  host [nrec][nsteps] FP64 (nullable when nrec = 0)
+ *   cg_iters_out host, nullable: CG iterations summed over the steps
+ * Host-driven like iga_multipatch_mass_solve; synchronous.  Errors: IGA_ERR_ARG,
+ * and the CG errors of iga_multipatch_mass_solve. */
+int iga_multipatch_leapfrog(const iga_multipatch* mp, int dtype, double dt, int nsteps, void* u,
+                            int src_patch, const double* src_s, double f0, double t0, double amp,
+                            int nrec, const int* rec_patch, const double* rec_s, double* traces,
+                            double cg_rtol, int cg_max_it, long long* cg_iters_out, void* stream);
+
 /* ---- misc ------------------------------------------------------------- */
 const char* iga_last_error(void);
 /* Number of library kernel launches issued since load (for launch accounting). */

@@ -104,3 +104,38 @@ def assemble_global(spaces, tables, maps, n_global):
         Al = stencil_to_csr(sp, T).tocoo()
         A = A + sps.csr_matrix((Al.data, (g[Al.row], g[Al.col])), shape=(n_global, n_global))
     return A.tocsr()
+
+
+def global_point_values(spaces, maps, n_global, patch, s):
+    """Global basis values at parametric point s of one patch: the patch's local values
+    B_i(s) placed at the global indices of its functions."""
+    from .wave import point_values
+    g = np.zeros(n_global)
+    g[maps[patch]] += point_values(spaces[patch], s)
+    return g
+
+
+def leapfrog_global(K, M, dt, u0, nsteps, source=None, receivers=(), rtol=1e-13, max_it=5000):
+    """Leapfrog on the global multi-patch matrices, the scheme of oracle.wave.Leapfrog
+    (u^{n+1} = 2 u^n - u^{n-1} + dt^2 a^n, M a^n = f^n - K u^n, u^1 = u^0 + dt^2/2 a^0,
+    Jacobi-PCG started at a^{n-1}).  source: (S, f0, t0, amp) with S the global point
+    values of the source; receivers: global point-value vectors.  Returns
+    (u^nsteps, traces[nrec, nsteps]) with traces[:, n] taken from u^{n+1}."""
+    from .wave import pcg, ricker
+    dinv = 1.0 / M.diagonal()
+    u = np.asarray(u0, dtype=np.float64).copy()
+    u_prev = None
+    a = np.zeros_like(u)
+    R = np.array(receivers).reshape(len(receivers), u.size)
+    traces = np.zeros((len(receivers), nsteps))
+    for n in range(nsteps):
+        f = np.zeros_like(u)
+        if source is not None:
+            S, f0, t0, amp = source
+            f = amp * ricker(n * dt, f0, t0) * S
+        a, _, _ = pcg(M, f - K @ u, a, dinv, rtol, max_it)
+        u_new = u + 0.5 * dt * dt * a if n == 0 else 2.0 * u - u_prev + dt * dt * a
+        u_prev, u = u, u_new
+        if len(receivers):
+            traces[:, n] = R @ u
+    return u, traces

@@ -184,4 +184,10 @@ inline void decode_offset(int t, int dim, int p, int delta[3]) {
         t /= P;
     }
 }
+// The (p+1)^d basis functions of a space that are non-zero at parametric point pt
+// (clamped to [0,1]^d): colex indices and values B_i(pt).  Host only.
+void point_basis(const iga_space* s, const double* pt, int* idx, double* w);
+// Ricker wavelet r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2).  Host only.
+double ricker(double t, double f0, double t0);
+
 }  // namespace iga

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "iga_internal.cuh"
+#include "leapfrog.cuh"
 
 struct iga_multipatch {
     std::vector<const iga_ops*> patches;
@@ -489,6 +490,149 @@ int mp_solve_typed(const iga_multipatch* mp, const T* b, T* x, int R, double rto
     return IGA_OK;
 }
 
+// ---------------------------------------------------------------- leapfrog
+// b = amp r(t_n) S - K~u (S: the source's global point values, FP64)
+template <typename T>
+__global__ void mpw_rhs_kernel(const T* __restrict__ ku, const double* __restrict__ src, double scale,
+                               T* __restrict__ b, long long G) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < G; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (T)((src ? scale * src[i] : 0.0) - (double)ku[i]);
+}
+// u^{n+1} into the u^{n-1} buffers: 2 u^n - u^{n-1} + dt^2 a^n, or u^0 + dt^2/2 a^0
+// on the first step.  FP32: the state is the unevaluated pair hi + lo.
+__global__ void mpw_update_kernel(const double* __restrict__ u, double* __restrict__ up, const double* __restrict__ a,
+                                  double c, int first, long long G) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < G; i += (long long)gridDim.x * blockDim.x)
+        up[i] = first ? u[i] + c * a[i] : 2.0 * u[i] - up[i] + c * a[i];
+}
+__global__ void mpw_update_kernel(const float* __restrict__ u, const float* __restrict__ ulo, float* __restrict__ up,
+                                  float* __restrict__ uplo, const float* __restrict__ a, float c, int first,
+                                  long long G) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < G; i += (long long)gridDim.x * blockDim.x) {
+        float hn, ln;
+        leapfrog_comp(u[i], ulo[i], up[i], uplo[i], __fmul_rn(c, a[i]), first != 0, hn, ln);
+        up[i] = hn;
+        uplo[i] = ln;
+    }
+}
+// traces[r][n] = sum_k w[r][k] (u + lo)[idx[r][k]]  (one thread per receiver)
+template <typename T>
+__global__ void mpw_receiver_kernel(const T* __restrict__ u, const T* __restrict__ ulo, const int* __restrict__ idx,
+                                    const double* __restrict__ w, int nrec, int nloc, double* __restrict__ traces,
+                                    int nsteps, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    double acc = 0.0;
+    for (int k = 0; k < nloc; ++k) {
+        const int j = idx[(size_t)r * nloc + k];
+        acc += w[(size_t)r * nloc + k] * ((double)u[j] + (ulo ? (double)ulo[j] : 0.0));
+    }
+    traces[(size_t)r * nsteps + n] = acc;
+}
+
+// Global point values of the basis at parametric point s of one patch: the patch's
+// non-zero local functions mapped to their global indices.
+void mp_point(const iga_multipatch* mp, int patch, const double* s, std::vector<int>& gidx, std::vector<double>& gw) {
+    const iga_space* sp = mp->patches[patch]->space;
+    int nloc = 1;
+    for (int d = 0; d < sp->dim; ++d) nloc *= sp->p + 1;
+    std::vector<int> idx(nloc);
+    std::vector<double> w(nloc);
+    point_basis(sp, s, idx.data(), w.data());
+    gidx.resize(nloc);
+    gw = w;
+    for (int k = 0; k < nloc; ++k) gidx[k] = (int)mp->l2g_h[mp->off[patch] + idx[k]];
+}
+
+template <typename T>
+int mp_leapfrog_typed(const iga_multipatch* mp, double dt, int nsteps, T* u_io, int src_patch, const double* src_s,
+                      double f0, double t0, double amp, int nrec, const int* rec_patch, const double* rec_s,
+                      double* traces_h, double rtol, int max_it, long long* iters_total, cudaStream_t st) {
+    const long long G = mp->G;
+    const bool comp = sizeof(T) == 4;
+    DevBuf bu, bup, blo, buplo, ba, bb, bku, bsrc, bridx, brw, btr;
+    int rc = bu.alloc(sizeof(T) * G);
+    if (!rc) rc = bup.alloc(sizeof(T) * G);
+    if (!rc) rc = ba.alloc(sizeof(T) * G);
+    if (!rc) rc = bb.alloc(sizeof(T) * G);
+    if (!rc) rc = bku.alloc(sizeof(T) * G);
+    if (!rc && comp) rc = blo.alloc(sizeof(T) * G);
+    if (!rc && comp) rc = buplo.alloc(sizeof(T) * G);
+    if (rc) return rc;
+    const int dim = mp->patches[0]->dim;
+    int nloc = 1;
+    for (int d = 0; d < dim; ++d) nloc *= mp->patches[0]->p + 1;
+    if (src_patch >= 0) {
+        std::vector<int> gi;
+        std::vector<double> gw, dense(G, 0.0);
+        mp_point(mp, src_patch, src_s, gi, gw);
+        for (size_t k = 0; k < gi.size(); ++k) dense[gi[k]] += gw[k];
+        if ((rc = bsrc.alloc(sizeof(double) * G))) return rc;
+        IGA_CUDA(cudaMemcpyAsync(bsrc.ptr, dense.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
+        IGA_CUDA(cudaStreamSynchronize(st));
+    }
+    if (nrec > 0) {
+        std::vector<int> ri((size_t)nrec * nloc);
+        std::vector<double> rw((size_t)nrec * nloc);
+        for (int r = 0; r < nrec; ++r) {
+            std::vector<int> gi;
+            std::vector<double> gw;
+            mp_point(mp, rec_patch[r], rec_s + (size_t)r * dim, gi, gw);
+            std::copy(gi.begin(), gi.end(), ri.begin() + (size_t)r * nloc);
+            std::copy(gw.begin(), gw.end(), rw.begin() + (size_t)r * nloc);
+        }
+        if ((rc = bridx.alloc(sizeof(int) * ri.size())) || (rc = brw.alloc(sizeof(double) * rw.size())) ||
+            (rc = btr.alloc(sizeof(double) * (size_t)nrec * nsteps)))
+            return rc;
+        IGA_CUDA(cudaMemcpyAsync(bridx.ptr, ri.data(), sizeof(int) * ri.size(), cudaMemcpyHostToDevice, st));
+        IGA_CUDA(cudaMemcpyAsync(brw.ptr, rw.data(), sizeof(double) * rw.size(), cudaMemcpyHostToDevice, st));
+        IGA_CUDA(cudaStreamSynchronize(st));
+    }
+    T* u = bu.as<T>();
+    T* up = bup.as<T>();
+    T* ulo = comp ? blo.as<T>() : nullptr;
+    T* uplo = comp ? buplo.as<T>() : nullptr;
+    IGA_CUDA(cudaMemcpyAsync(u, u_io, sizeof(T) * G, cudaMemcpyDeviceToDevice, st));
+    IGA_CUDA(cudaMemsetAsync(ba.ptr, 0, sizeof(T) * G, st));
+    if (comp) IGA_CUDA(cudaMemsetAsync(ulo, 0, sizeof(T) * G, st));
+    const int grid = (int)std::min<long long>((G + 255) / 256, kMpBlocks);
+    *iters_total = 0;
+    for (int n = 0; n < nsteps; ++n) {
+        MpWork w;
+        if ((rc = mp_work(mp, sizeof(T), 1, w))) return rc;
+        if ((rc = mp_apply_typed<T>(mp, IGA_OP_K, u, bku.as<T>(), 1, st, w))) return rc;
+        mpw_rhs_kernel<T><<<grid, 256, 0, st>>>(bku.as<T>(), src_patch >= 0 ? bsrc.as<double>() : nullptr,
+                                               amp * ricker(n * dt, f0, t0), bb.as<T>(), G);
+        IGA_LAUNCH_CHECK("mpw_rhs_kernel");
+        int it = 0;
+        double rel = 0.0;
+        // a^n from the multi-patch PCG started at a^{n-1}
+        if ((rc = mp_solve_typed<T>(mp, bb.as<T>(), ba.as<T>(), 1, rtol, max_it, &it, &rel, st))) return rc;
+        *iters_total += it;
+        if constexpr (sizeof(T) == 8) {
+            mpw_update_kernel<<<grid, 256, 0, st>>>((const double*)u, (double*)up, (const double*)ba.ptr,
+                                                    (n == 0 ? 0.5 : 1.0) * dt * dt, n == 0, G);
+        } else {
+            mpw_update_kernel<<<grid, 256, 0, st>>>((const float*)u, (const float*)ulo, (float*)up, (float*)uplo,
+                                                    (const float*)ba.ptr, (float)((n == 0 ? 0.5 : 1.0) * dt * dt),
+                                                    n == 0, G);
+        }
+        IGA_LAUNCH_CHECK("mpw_update_kernel");
+        std::swap(u, up);
+        std::swap(ulo, uplo);
+        if (nrec > 0) {
+            mpw_receiver_kernel<T><<<(nrec + 127) / 128, 128, 0, st>>>(u, ulo, bridx.as<int>(), brw.as<double>(), nrec,
+                                                                     nloc, btr.as<double>(), nsteps, n);
+            IGA_LAUNCH_CHECK("mpw_receiver_kernel");
+        }
+    }
+    IGA_CUDA(cudaMemcpyAsync(u_io, u, sizeof(T) * G, cudaMemcpyDeviceToDevice, st));
+    if (nrec > 0)
+        IGA_CUDA(cudaMemcpyAsync(traces_h, btr.ptr, sizeof(double) * (size_t)nrec * nsteps, cudaMemcpyDeviceToHost, st));
+    IGA_CUDA(cudaStreamSynchronize(st));
+    return IGA_OK;
+}
+
 }  // namespace
 }  // namespace iga
 
@@ -520,4 +664,29 @@ extern "C" int iga_multipatch_mass_solve(const iga_multipatch* mp, int dtype, co
     return dtype == IGA_F64
                ? mp_solve_typed<double>(mp, (const double*)b, (double*)x, nrhs, rtol, max_it, iters_out, relres_out, st)
                : mp_solve_typed<float>(mp, (const float*)b, (float*)x, nrhs, rtol, max_it, iters_out, relres_out, st);
+}
+
+extern "C" int iga_multipatch_leapfrog(const iga_multipatch* mp, int dtype, double dt, int nsteps, void* u,
+                                       int src_patch, const double* src_s, double f0, double t0, double amp,
+                                       int nrec, const int* rec_patch, const double* rec_s, double* traces,
+                                       double cg_rtol, int cg_max_it, long long* cg_iters_out, void* stream) {
+    if (!mp || !u) return fail(IGA_ERR_ARG, "null argument");
+    if (dtype != IGA_F32 && dtype != IGA_F64) return fail(IGA_ERR_ARG, "dtype must be IGA_F32 or IGA_F64");
+    if (!(dt > 0.0) || nsteps < 1 || cg_max_it < 1 || !(cg_rtol >= 0.0))
+        return fail(IGA_ERR_ARG, "bad dt / nsteps / cg_max_it / cg_rtol");
+    const int npatch = (int)mp->patches.size();
+    if (src_patch >= npatch || (src_patch >= 0 && !src_s)) return fail(IGA_ERR_ARG, "bad source");
+    if (nrec < 0 || (nrec > 0 && (!rec_patch || !rec_s || !traces))) return fail(IGA_ERR_ARG, "bad receivers");
+    for (int r = 0; r < nrec; ++r)
+        if (rec_patch[r] < 0 || rec_patch[r] >= npatch) return fail(IGA_ERR_ARG, "receiver patch does not exist");
+    if (mp->G > (1LL << 31) - 1) return fail(IGA_ERR_ARG, "too many global functions");
+    long long iters = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rc = dtype == IGA_F64
+                       ? mp_leapfrog_typed<double>(mp, dt, nsteps, (double*)u, src_patch, src_s, f0, t0, amp, nrec,
+                                                   rec_patch, rec_s, traces, cg_rtol, cg_max_it, &iters, st)
+                       : mp_leapfrog_typed<float>(mp, dt, nsteps, (float*)u, src_patch, src_s, f0, t0, amp, nrec,
+                                                  rec_patch, rec_s, traces, cg_rtol, cg_max_it, &iters, st);
+    if (cg_iters_out) *cg_iters_out = iters;
+    return rc;
 }

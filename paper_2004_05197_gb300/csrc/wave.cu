@@ -108,7 +108,7 @@ __global__ void pulse_kernel(GeomParams gp, const double* __restrict__ greville,
 }
 
 // Basis functions non-zero at parametric point s: global indices and values B_i(s).
-static void point_basis(const iga_space* s, const double* pt, int* idx, double* w) {
+void point_basis(const iga_space* s, const double* pt, int* idx, double* w) {
     const int p = s->p, P1 = p + 1;
     std::vector<double> vals[3];
     int first[3] = {0, 0, 0};
@@ -174,7 +174,7 @@ static int force_dispatch(const iga_wave* w, cudaStream_t st) {
     return fail(IGA_ERR_ARG, "unsupported (dim, p)");
 }
 
-static double ricker(double t, double f0, double t0) {
+double ricker(double t, double f0, double t0) {
     const double a = (3.14159265358979323846 * f0 * (t - t0)) * (3.14159265358979323846 * f0 * (t - t0));
     return (1.0 - 2.0 * a) * std::exp(-a);
 }

@@ -41,7 +41,8 @@ EXPORTED = [
     "iga_batch_create", "iga_batch_destroy", "iga_batch_step", "iga_batch_tune", "iga_batch_partition",
     "iga_mass_solve_noalloc", "iga_sampling_length_for_mesh",
     "iga_multipatch_create", "iga_multipatch_destroy", "iga_multipatch_size", "iga_multipatch_global_index",
-    "iga_multipatch_apply", "iga_multipatch_mass_solve", "iga_ops_set_path", "iga_ops_brick_info",
+    "iga_multipatch_apply", "iga_multipatch_mass_solve", "iga_multipatch_leapfrog", "iga_ops_set_path",
+    "iga_ops_brick_info",
     "iga_barrier_selftest",
 ]
 
@@ -117,6 +118,8 @@ _sig = {
     "iga_multipatch_global_index": [_vp, _i, C.POINTER(C.c_longlong)],
     "iga_multipatch_apply": [_vp, _i, _i, _vp, _vp, _i, _vp],
     "iga_multipatch_mass_solve": [_vp, _i, _vp, _vp, _i, _d, _i, C.POINTER(_i), C.POINTER(_d), _vp],
+    "iga_multipatch_leapfrog": [_vp, _i, _d, _i, _vp, _i, C.POINTER(_d), _d, _d, _d, _i, C.POINTER(_i),
+                                C.POINTER(_d), C.POINTER(_d), _d, _i, C.POINTER(C.c_longlong), _vp],
     "iga_sampling_length_for_mesh": [_d, _i, _i, _d, _d, _d, _d, C.POINTER(_i)],
     "iga_mass_solve_noalloc": [_vp, _i, _vp, _vp, _i, _d, _i, _u, C.POINTER(_i), C.POINTER(_d), _vp],
     "iga_wave_create": [_vp, C.POINTER(iga_wave_desc), C.POINTER(_vp)],
@@ -334,6 +337,30 @@ def iga_multipatch_mass_solve(mp, dtype, b, x, nrhs, rtol, max_it, stream=None, 
     rc = _check(_lib.iga_multipatch_mass_solve(mp, dtype, _dptr(b), _dptr(x), nrhs, rtol, max_it, iters, rel,
                                                _stream(stream)), ok)
     return rc, np.array(iters[:]), np.array(rel[:])
+
+
+def iga_multipatch_leapfrog(mp, dtype, dt, nsteps, u, src_patch=-1, src_s=None, f0=10.0, t0=0.1, amp=1.0,
+                            rec_patch=(), rec_s=None, cg_rtol=1e-10, cg_max_it=1000, stream=None):
+    """u: device [n_global] (u^0 in, u^nsteps out); src_s: [dim]; rec_patch: [nrec];
+    rec_s: [nrec][dim].  Returns (traces [nrec][nsteps], CG iterations summed over steps)."""
+    nrec = len(rec_patch)
+    keep = []
+    sp = C.POINTER(C.c_double)()
+    if src_s is not None:
+        a, sp = _host_f64(np.asarray(src_s, dtype=np.float64).ravel())
+        keep.append(a)
+    rp = (C.c_int * max(1, nrec))(*[int(r) for r in rec_patch])
+    rs = C.POINTER(C.c_double)()
+    if nrec:
+        a, rs = _host_f64(np.asarray(rec_s, dtype=np.float64).ravel())
+        keep.append(a)
+    tr = np.zeros((nrec, nsteps), dtype=np.float64)
+    it = C.c_longlong(0)
+    _check(_lib.iga_multipatch_leapfrog(mp, dtype, dt, nsteps, _dptr(u), src_patch, sp, f0, t0, amp, nrec, rp, rs,
+                                        tr.ctypes.data_as(C.POINTER(C.c_double)), cg_rtol, cg_max_it, C.byref(it),
+                                        _stream(stream)))
+    del keep
+    return tr, it.value
 
 
 # ---- waves ---------------------------------------------------------------------

@@ -105,3 +105,24 @@ def test_p1_eight_boxes_equal_the_single_patch():
     assert np.abs(M.sum() - 1.0) <= 1e-13
     assert np.abs(K - K1).max() <= 1e-12 * np.abs(K1).max()
     assert np.abs(M - M1).max() <= 1e-13 * np.abs(M1).max()
+
+
+def test_global_leapfrog_equals_the_single_patch_leapfrog():
+    """With one patch and no interface the global leapfrog is the single-patch oracle
+    leapfrog (pinned by its own tests): same steps, sources, receivers and traces."""
+    from oracle.geometry import AnnulusSector
+    from oracle.multipatch import global_point_values, leapfrog_global
+    from oracle.wave import Leapfrog
+    sp = Space(2, 2, 10, AnnulusSector(), ConstCoef(1.0))
+    SK, SM = true_rows(sp, sp.all_rows())
+    maps, G = global_numbering([sp.m], [], dim=2)
+    K, M = stencil_to_csr(sp, SK), stencil_to_csr(sp, SM)
+    dt, nsteps = 0.01, 25
+    src, rec = (0.4, 0.6), [(0.5, 0.5), (0.2, 0.9)]
+    lf = Leapfrog(sp, SK, SM, dt, rtol=1e-14, max_it=2000)
+    u_ref, _, tr_ref = lf.run(np.zeros(sp.N), nsteps, sources=[(src, 10.0, 0.1, 2.0)], receivers=rec)
+    S = global_point_values([sp], maps, G, 0, src)
+    R = [global_point_values([sp], maps, G, 0, r) for r in rec]
+    u, tr = leapfrog_global(K, M, dt, np.zeros(G), nsteps, source=(S, 10.0, 0.1, 2.0), receivers=R, rtol=1e-14)
+    assert np.abs(u[maps[0]] - u_ref).max() <= 1e-12 * np.abs(u_ref).max()
+    assert np.abs(tr - tr_ref).max() <= 1e-12 * np.abs(u_ref).max()
