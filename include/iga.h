@@ -487,9 +487,10 @@ int iga_multipatch_apply(const iga_multipatch* mp, int which, int dtype, const v
                          int nrhs, void* stream);
 /* Jacobi-PCG on the global M~ a = b, b / x device [nrhs][n_global] (x: initial guess
  * in, solution out), stop when ||r||_2 <= rtol ||b||_2; FP32 dtype: FP32 vectors,
- * FP64 residual and dot products.  Host-driven (plain schedule: scalars read back
- * every iteration), synchronous.  Returns IGA_ERR_NOT_CONVERGED / IGA_ERR_NONFINITE
- * as mass_solve. */
+ * FP64 residual and dot products.  The CG scalars stay on the device; the host
+ * reads them back every 16 iterations to test convergence (a right-hand side that
+ * converges inside such a batch stops changing at once).  Synchronous.  Returns
+ * IGA_ERR_NOT_CONVERGED / IGA_ERR_NONFINITE as mass_solve. */
 int iga_multipatch_mass_solve(const iga_multipatch* mp, int dtype, const void* b, void* x, int nrhs,
                               double rtol, int max_it, int* iters_out, double* relres_out,
                               void* stream);

@@ -7,8 +7,9 @@
 // Applied matrix-free: gather the patch-local vectors, apply every patch's
 // stencil operator with the single-patch kernels, and sum the patch results of
 // every global function in a fixed order (a function on a shared side belongs
-// to two or more patches).  The mass solve is Jacobi-PCG on the global system,
-// host-driven (two scalar read-backs per iteration): the plain schedule.
+// to two or more patches).  The mass solve is Jacobi-PCG on the global system
+// with its scalars on the device; the host checks convergence every kMpCheck
+// iterations.
 //
 // Global numbering: local functions visited patch by patch, each patch in
 // colexicographic order; the side functions identified by the interfaces (sides
@@ -113,6 +114,7 @@ __global__ void mp_diag_kernel(const double* const* __restrict__ fm, const int* 
 
 constexpr int kMpThreads = 256;
 constexpr int kMpBlocks = 152 * 8;
+constexpr int kMpCheck = 16;   // CG iterations between host checks of the multi-patch solve
 
 // per-block FP64 partial sums of K dot products over [R][G] vectors (fixed order)
 template <int K>
@@ -209,6 +211,72 @@ __global__ void mp_reduce_kernel(const double* __restrict__ partials, int nb, do
         double s = 0.0;
         for (int q = 0; q < kMpThreads / 32; ++q) s += ws[q][threadIdx.x];
         out[threadIdx.x] = s;
+    }
+}
+
+// CG scalars of one right-hand side, kept on the device between host checks
+struct MpScal {
+    double rz, rr, bn, alpha, beta;
+    int active, iters, brk, pad;
+};
+// alpha = (r, z) / (p, M p) for every active right-hand side (breakdown: inactive, brk)
+__global__ void mp_alpha_kernel(MpScal* sc, const double* __restrict__ red, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !sc[r].active) return;
+    const double pq = red[3 * r];
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        sc[r].brk = 1;
+        sc[r].active = 0;
+        sc[r].alpha = 0.0;
+        return;
+    }
+    sc[r].alpha = sc[r].rz / pq;
+}
+// after the update: count the iteration, test ||r|| <= rtol ||b||, else beta
+__global__ void mp_beta_kernel(MpScal* sc, const double* __restrict__ red, double rtol, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !sc[r].active) return;
+    sc[r].iters += 1;
+    sc[r].rr = red[3 * r];
+    const double rz_new = red[3 * r + 1];
+    if (rtol > 0.0 && sqrt(sc[r].rr) <= rtol * sc[r].bn) {
+        sc[r].active = 0;
+        return;
+    }
+    sc[r].beta = rz_new / sc[r].rz;
+    sc[r].rz = rz_new;
+}
+// the update with alpha from the device (no work, zero partials, once inactive)
+template <typename T>
+__global__ void __launch_bounds__(kMpThreads) mp_update_dev_kernel(T* x, double* res, T* z, const T* __restrict__ p,
+                                                                   const T* __restrict__ q, const T* __restrict__ dinv,
+                                                                   long long G, int r, const MpScal* sc,
+                                                                   double* partials) {
+    double v[2] = {0.0, 0.0};
+    if (sc[r].active) {
+        const double alpha = sc[r].alpha;
+        for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G;
+             g += (long long)gridDim.x * blockDim.x) {
+            const long long o = (long long)r * G + g;
+            x[o] = x[o] + (T)alpha * p[o];
+            const double ri = res[o] - alpha * (double)q[o];
+            res[o] = ri;
+            const T zi = (T)((double)dinv[g] * ri);
+            z[o] = zi;
+            v[0] += ri * ri;
+            v[1] += ri * (double)zi;
+        }
+    }
+    mp_block_partials<2>(v, partials);
+}
+// p = z + beta p while active
+template <typename T>
+__global__ void mp_dir_dev_kernel(T* p, const T* __restrict__ z, long long G, int r, const MpScal* sc) {
+    if (!sc[r].active) return;
+    const double beta = sc[r].beta;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const long long o = (long long)r * G + g;
+        p[o] = z[o] + (T)beta * p[o];
     }
 }
 
@@ -352,12 +420,13 @@ namespace {
 struct MpWork {
     void *xl, *yl, *z, *p, *q;
     double *res, *partials, *red;
+    MpScal* scal;
 };
 
 size_t mp_work_bytes(const iga_multipatch* mp, size_t es, int R) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     return 2 * up(es * R * mp->L) + up(8 * (size_t)R * mp->G) + 3 * up(es * R * mp->G) + up(8 * kMpBlocks * 3) +
-           up(8 * 3 * (size_t)R) + 256;
+           up(8 * 3 * (size_t)R) + up(64 * (size_t)R) + 256;
 }
 
 int mp_work(const iga_multipatch* mp, size_t es, int R, MpWork& w) {
@@ -381,6 +450,7 @@ int mp_work(const iga_multipatch* mp, size_t es, int R, MpWork& w) {
     w.q = take(es * R * mp->G);
     w.partials = (double*)take(8 * kMpBlocks * 3);
     w.red = (double*)take(8 * 3 * (size_t)R);
+    w.scal = (MpScal*)take(64 * (size_t)R);
     return IGA_OK;
 }
 
@@ -438,45 +508,53 @@ int mp_solve_typed(const iga_multipatch* mp, const T* b, T* x, int R, double rto
         active[r] = bn[r] > 0.0 && !(rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]);
         if (!(bn[r] > 0.0)) IGA_CUDA(cudaMemsetAsync(x + (size_t)r * G, 0, sizeof(T) * G, st));
     }
-    for (int it = 0; it < max_it; ++it) {
+    // iterations with the scalars on the device; the host reads them back every
+    // kMpCheck iterations (a right-hand side that converges inside a batch stops
+    // changing at once: its kernels see active = 0)
+    std::vector<MpScal> sc(R);
+    for (int r = 0; r < R; ++r) {
+        sc[r] = MpScal{rz[r], rr[r], bn[r], 0.0, 0.0, active[r], 0, 0, 0};
+    }
+    IGA_CUDA(cudaMemcpyAsync(w.scal, sc.data(), sizeof(MpScal) * R, cudaMemcpyHostToDevice, st));
+    const int sgrid = (R + 31) / 32;
+    for (int it = 0; it < max_it;) {
         bool any = false;
-        for (int r = 0; r < R; ++r) any = any || active[r];
+        for (int r = 0; r < R; ++r) any = any || sc[r].active;
         if (!any) break;
-        if ((rc = mp_apply_typed<T>(mp, IGA_OP_M, p, q, R, st, w))) return rc;
-        for (int r = 0; r < R; ++r) {
-            if (!active[r]) continue;
-            mp_dot_kernel<T><<<grid, kMpThreads, 0, st>>>(p, q, G, r, w.partials);
-            IGA_LAUNCH_CHECK("mp_dot_kernel");
-            mp_reduce_kernel<1><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
-            IGA_LAUNCH_CHECK("mp_reduce_kernel");
-        }
-        if ((rc = reduce_all())) return rc;
-        std::vector<double> alpha(R, 0.0);
-        for (int r = 0; r < R; ++r) {
-            if (!active[r]) continue;
-            const double pq = red[3 * r];
-            if (!(pq > 0.0) || !std::isfinite(pq)) return fail(IGA_ERR_NONFINITE, "CG breakdown: (p, M p) <= 0 or non-finite");
-            alpha[r] = rz[r] / pq;
-            mp_update_kernel<T><<<grid, kMpThreads, 0, st>>>(x, w.res, z, p, q, dinv, G, r, alpha[r], w.partials);
-            IGA_LAUNCH_CHECK("mp_update_kernel");
-            mp_reduce_kernel<2><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
-            IGA_LAUNCH_CHECK("mp_reduce_kernel");
-        }
-        if ((rc = reduce_all())) return rc;
-        for (int r = 0; r < R; ++r) {
-            if (!active[r]) continue;
-            iters[r] += 1;
-            rr[r] = red[3 * r];
-            const double rz_new = red[3 * r + 1];
-            if (rtol > 0.0 && std::sqrt(rr[r]) <= rtol * bn[r]) {
-                active[r] = 0;
-                continue;
+        const int nb = std::min(kMpCheck, max_it - it);
+        for (int k = 0; k < nb; ++k) {
+            if ((rc = mp_apply_typed<T>(mp, IGA_OP_M, p, q, R, st, w))) return rc;
+            for (int r = 0; r < R; ++r) {
+                mp_dot_kernel<T><<<grid, kMpThreads, 0, st>>>(p, q, G, r, w.partials);
+                IGA_LAUNCH_CHECK("mp_dot_kernel");
+                mp_reduce_kernel<1><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
+                IGA_LAUNCH_CHECK("mp_reduce_kernel");
             }
-            const double beta = rz_new / rz[r];
-            rz[r] = rz_new;
-            mp_dir_kernel<T><<<grid, kMpThreads, 0, st>>>(p, z, G, r, beta);
-            IGA_LAUNCH_CHECK("mp_dir_kernel");
+            mp_alpha_kernel<<<sgrid, 32, 0, st>>>(w.scal, w.red, R);
+            IGA_LAUNCH_CHECK("mp_alpha_kernel");
+            for (int r = 0; r < R; ++r) {
+                mp_update_dev_kernel<T><<<grid, kMpThreads, 0, st>>>(x, w.res, z, p, q, dinv, G, r, w.scal,
+                                                                     w.partials);
+                IGA_LAUNCH_CHECK("mp_update_dev_kernel");
+                mp_reduce_kernel<2><<<1, kMpThreads, 0, st>>>(w.partials, grid, w.red + 3 * r);
+                IGA_LAUNCH_CHECK("mp_reduce_kernel");
+            }
+            mp_beta_kernel<<<sgrid, 32, 0, st>>>(w.scal, w.red, rtol, R);
+            IGA_LAUNCH_CHECK("mp_beta_kernel");
+            for (int r = 0; r < R; ++r) {
+                mp_dir_dev_kernel<T><<<grid, kMpThreads, 0, st>>>(p, z, G, r, w.scal);
+                IGA_LAUNCH_CHECK("mp_dir_dev_kernel");
+            }
         }
+        it += nb;
+        IGA_CUDA(cudaMemcpyAsync(sc.data(), w.scal, sizeof(MpScal) * R, cudaMemcpyDeviceToHost, st));
+        IGA_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r)
+            if (sc[r].brk) return fail(IGA_ERR_NONFINITE, "CG breakdown: (p, M p) <= 0 or non-finite");
+    }
+    for (int r = 0; r < R; ++r) {
+        rr[r] = sc[r].rr;
+        iters[r] = sc[r].iters;
     }
     bool nc = false;
     for (int r = 0; r < R; ++r) {
