@@ -437,9 +437,10 @@ def fp64_forms_and_error(ctx, args):
     """Single-shot FP64 forms of the bench workload beside the FP32 persistent form.
 
     * FP64 with the plain CG schedule (a host round trip per CG iteration), with the
-      graph schedule (phase launches in a CUDA graph, convergence on the device) and with
-      the persistent schedule: shot-steps/s, the first two on `compare_steps` steps, the
-      persistent one on all steps of the workload;
+      graph schedule (phase launches in a CUDA graph, convergence on the device), by
+      iterative refinement around the FP32 solver (IGA_SOLVE_REFINE: FP64 residual and
+      stopping rule, FP32 corrections) and with the persistent schedule: shot-steps/s,
+      the first three on `compare_steps` steps, the persistent one on all steps;
     * FP32 error: relative L2 distance of the FP32 state after all steps (the final state
       of the timed FP32 pass) from the FP64 persistent state after the same steps (CG
       rtol 1e-10).  The FP64 waves are pinned to the oracle by the wave parity tests.
@@ -454,6 +455,7 @@ def fp64_forms_and_error(ctx, args):
     u64 = None
     for name, flags, P in (("plain", iga.IGA_SOLVE_PLAIN, min(args.compare_steps, nsteps)),
                            ("graph", iga.IGA_SOLVE_GRAPH, min(args.compare_steps, nsteps)),
+                           ("refine", iga.IGA_SOLVE_REFINE, min(args.compare_steps, nsteps)),
                            ("persistent", 0, nsteps)):
         w64 = iga.iga_wave_create(ops, 1, iga.IGA_F64, dt, src_pos=src, f0=10.0, t0=0.1, cg_rtol=1e-10,
                                   cg_max_it=args.cg_max_it, solve_flags=flags, cg_guess=args.cg_guess)
@@ -476,7 +478,7 @@ def fp64_forms_and_error(ctx, args):
     res["fp32_vs_fp64_rel_l2_error"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
     res["fp32_vs_fp64_steps"] = nsteps
     fastest = max(res["fp64_plain_shot_steps_per_s"], res["fp64_graph_shot_steps_per_s"],
-                  res["fp64_persistent_shot_steps_per_s"])
+                  res["fp64_refine_shot_steps_per_s"], res["fp64_persistent_shot_steps_per_s"])
     res["fp64_fastest_single_shot_shot_steps_per_s"] = fastest
     return res
 
