@@ -366,6 +366,8 @@ def _wave_case(dtype, nsteps=20):
 def test_wave_fp64_matches_oracle():
     u, ur, tr, trr = _wave_case(iga.IGA_F64)
     assert np.linalg.norm(u - ur) <= 1e-11 * np.linalg.norm(ur)
+    # every coefficient, not only the L2 norm of the state
+    assert np.abs(u - ur).max() <= 1e-11 * np.abs(ur).max()
     # a trace is a weighted sum of (p+1)^d coefficients: compare on the field's scale
     assert np.abs(tr - trr).max() <= 1e-11 * np.abs(ur).max()
 
@@ -375,6 +377,8 @@ def test_wave_fp32_error_against_fp64_oracle():
     err = np.linalg.norm(u - ur) / np.linalg.norm(ur)
     print("FP32 leapfrog relative L2 error after 20 steps:", err)
     assert err <= 1e-5
+    assert np.abs(u - ur).max() <= 2e-5 * np.abs(ur).max()
+    assert np.abs(tr - trr).max() <= 2e-5 * np.abs(ur).max()
 
 
 @pytest.mark.parametrize("mode", ["f64", "f64_plain", "f64_graph", "f32", "f32_graph", "f64_guess2", "f32_guess2",
