@@ -26,6 +26,7 @@
 
 #include "geom.cuh"
 #include "quad.cuh"
+#include "dfloat.cuh"
 #include "stencil.cuh"
 #include "host_bspline.h"
 #include "iga_internal.cuh"
@@ -33,6 +34,10 @@
 namespace iga {
 
 // ---------------------------------------------------------------- a3: band elements
+// Geometry, coefficient and the pulled-back weights at every Gauss point in FP64;
+// the basis products, G grad phi and the element contractions in double-float
+// pairs (dfloat.cuh: about 48 significant bits, on the FP32 pipe).  An entry is
+// the FP64 sum hi + lo of its pair.
 template <int DIM, int P>
 __global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double* __restrict__ fK,
                             double* __restrict__ fM, long long pitch, int lo, int hi, int all_true,
@@ -43,12 +48,14 @@ __global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double
     int nqd = nq;
 #pragma unroll
     for (int k = 1; k < DIM; ++k) nqd *= nq;
-    double* Gq = sm;                          // [nqd][NS]
-    double* wq = Gq + nqd * S::NS;            // [nqd]
-    double* grad = wq + nqd;                  // [NLOC][nqd][DIM]
-    double* Ggrad = grad + S::NLOC * nqd * DIM;
-    double* val = Ggrad + S::NLOC * nqd * DIM;   // [NLOC][nqd]
-    double* vw = val + S::NLOC * nqd;            // [NLOC][nqd]
+    f2* Gq = reinterpret_cast<f2*>(sm);   // [nqd][NS]
+    f2* wq = Gq + nqd * S::NS;            // [nqd]
+    f2* grad = wq + nqd;                  // [NLOC][nqd][DIM]
+    f2* Ggrad = grad + S::NLOC * nqd * DIM;
+    f2* val = Ggrad + S::NLOC * nqd * DIM;   // [NLOC][nqd]
+    f2* vw = val + S::NLOC * nqd;            // [NLOC][nqd]
+    const f2* bv2 = reinterpret_cast<const f2*>(gp.bval2);
+    const f2* bd2 = reinterpret_cast<const f2*>(gp.bder2);
 
     int e[3] = {0, 0, 0};
     decode<DIM>(elems[blockIdx.x], gp.n_el, e);
@@ -59,8 +66,8 @@ __global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double
         const double det = qp_weights(gp, e, g, G, wm);
         if (!(det > 0.0)) atomicOr(status, 2);
 #pragma unroll
-        for (int k = 0; k < S::NS; ++k) Gq[q * S::NS + k] = G[k];
-        wq[q] = wm;
+        for (int k = 0; k < S::NS; ++k) Gq[q * S::NS + k] = df_from(G[k]);
+        wq[q] = df_from(wm);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < S::NLOC * nqd; idx += blockDim.x) {
@@ -68,16 +75,35 @@ __global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double
         int g[3] = {0, 0, 0}, al[3] = {0, 0, 0};
         decode<DIM>(q, nq, g);
         decode<DIM>(a, P + 1, al);
-        double gr[DIM], v, Gg[DIM];
-        local_basis<DIM, P>(gp, e, g, al, gr, v);
-        sym_matvec<DIM>(Gq + q * S::NS, gr, Gg);
+        f2 v[DIM], dv[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            grad[(a * nqd + q) * DIM + k] = gr[k];
-            Ggrad[(a * nqd + q) * DIM + k] = Gg[k];
+            const int t = (e[k] * nq + g[k]) * (P + 1) + al[k];
+            v[k] = bv2[t];
+            dv[k] = bd2[t];
         }
-        val[a * nqd + q] = v;
-        vw[a * nqd + q] = v * wq[q];
+        f2 vv = v[0], gr[DIM];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) vv = df_mul(vv, v[k]);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            f2 gk = k == 0 ? dv[0] : v[0];
+#pragma unroll
+            for (int j = 1; j < DIM; ++j) gk = df_mul(gk, j == k ? dv[j] : v[j]);
+            gr[k] = gk;
+        }
+        // G grad phi with G packed symmetric
+        const f2* Gp = Gq + q * S::NS;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            f2 acc = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < DIM; ++l) df_mac(acc, Gp[sym_index(DIM, k, l)], gr[l]);
+            Ggrad[(a * nqd + q) * DIM + k] = acc;
+            grad[(a * nqd + q) * DIM + k] = gr[k];
+        }
+        val[a * nqd + q] = vv;
+        vw[a * nqd + q] = df_mul(vv, wq[q]);
     }
     __syncthreads();
     const int m = gp.m;
@@ -97,14 +123,14 @@ __global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double
         if (!all_true && in_range<DIM>(i, lo, hi) && in_range<DIM>(j, lo, hi)) continue;  // surrogate slot
         long long li = 0;
         for (int k = DIM - 1; k >= 0; --k) li = li * m + i[k];
-        double kv = 0.0, mv = 0.0;
+        f2 kv = {0.f, 0.f}, mv = {0.f, 0.f};
         for (int q = 0; q < nqd; ++q) {
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) kv += Ggrad[(a * nqd + q) * DIM + k] * grad[(b * nqd + q) * DIM + k];
-            mv += vw[a * nqd + q] * val[b * nqd + q];
+            for (int k = 0; k < DIM; ++k) df_mac(kv, Ggrad[(a * nqd + q) * DIM + k], grad[(b * nqd + q) * DIM + k]);
+            df_mac(mv, vw[a * nqd + q], val[b * nqd + q]);
         }
-        if (t > S::T0) fK[(size_t)(t - S::T0 - 1) * pitch + li] += kv;
-        fM[(size_t)(t - S::T0) * pitch + li] += mv;
+        if (t > S::T0) fK[(size_t)(t - S::T0 - 1) * pitch + li] += df_value(kv);
+        fM[(size_t)(t - S::T0) * pitch + li] += df_value(mv);
     }
 }
 

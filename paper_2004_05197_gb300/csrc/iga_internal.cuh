@@ -52,6 +52,8 @@ struct GeomParams {
     const double* qw;      // [nq] Gauss weight times h
     const double* bval;    // [n_el][nq][p+1] values of local functions e+a at point g
     const double* bder;    // [n_el][nq][p+1] derivatives
+    const float* bval2;    // the two tables as FP32 pairs (hi, lo) per entry
+    const float* bder2;
     const int* tspan;      // [n_el][nq] first theta function non-zero at the point
     const double* tval;    // [n_el][nq][theta_deg+1] theta basis values at the point
 };
@@ -114,7 +116,7 @@ struct iga_space {
     std::vector<double> qs_h;               // [n_el][nq] Gauss point coordinates (host copy)
     std::vector<int> tspan_h;               // [n_el][nq] first non-zero theta function (host copy)
     std::vector<double> tval_h;             // [n_el][nq][theta_deg+1] theta basis values (host copy)
-    iga::DevBuf theta, qs, qw, bval, bder, tspan, tval;
+    iga::DevBuf theta, qs, qw, bval, bder, bval2, bder2, tspan, tval;
     iga::GeomParams gp;
     // element lists of the band quadrature, grouped by colour, built on the first
     // assembly that needs them ([0]: boundary band, [1]: every element)

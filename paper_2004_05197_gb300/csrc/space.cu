@@ -138,6 +138,17 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
     if (!rc) rc = upload(s->qw, qw);
     if (!rc) rc = upload(s->bval, bval);
     if (!rc) rc = upload(s->bder, bder);
+    {   // FP32 pairs hi + lo of the tables (the band quadrature's double-float path)
+        std::vector<float> bv2(2 * bval.size()), bd2(2 * bder.size());
+        for (size_t i = 0; i < bval.size(); ++i) {
+            bv2[2 * i] = (float)bval[i];
+            bv2[2 * i + 1] = (float)(bval[i] - (double)bv2[2 * i]);
+            bd2[2 * i] = (float)bder[i];
+            bd2[2 * i + 1] = (float)(bder[i] - (double)bd2[2 * i]);
+        }
+        if (!rc) rc = upload(s->bval2, bv2);
+        if (!rc) rc = upload(s->bder2, bd2);
+    }
     std::vector<int> tspan(d.n_el * nq, 0);
     std::vector<double> tval;
     if (!rc && d.coef_kind == IGA_COEF_BSPLINE) {
@@ -188,6 +199,8 @@ extern "C" int iga_space_create(const iga_space_desc* desc, iga_space** out) {
     gp.qw = s->qw.as<double>();
     gp.bval = s->bval.as<double>();
     gp.bder = s->bder.as<double>();
+    gp.bval2 = s->bval2.as<float>();
+    gp.bder2 = s->bder2.as<float>();
     gp.tspan = s->tspan.as<int>();
     gp.tval = s->tval.as<double>();
     *out = s;
