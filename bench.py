@@ -952,7 +952,7 @@ def workload_config(args, world=1):
             "cg_schedule": args.solve,
             "cg_start": ("previous acceleration" if args.cg_guess == 0 else
                          "polynomial extrapolation in time, order %d" % args.cg_guess),
-            "precision": "FP32 fields/vectors/apply, FP64 quadrature, residual in FP64 (row kernels) or as an FP32 pair (brick PCG), compensated dot products",
+            "precision": "FP32 fields/vectors/apply, FP64 quadrature (band contractions in double-float FP32 pairs), residual in FP64 (row kernels) or as an FP32 pair (brick PCG), compensated dot products",
             "l2": "inputs larger than L2 (stencil fields %.2f GB)" % (D * pitch * 12 / 1e9),
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
