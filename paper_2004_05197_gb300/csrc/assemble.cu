@@ -135,6 +135,9 @@ __global__ void band_kernel(GeomParams gp, const int* __restrict__ elems, double
 }
 
 // ---------------------------------------------------------------- a2: sample rows
+// Per support element of the sample row: geometry, coefficient, weights and
+// G grad phi_a in FP64 at the Gauss points; the basis of every other local function
+// and the contraction over the points in double-float pairs (dfloat.cuh).
 template <int DIM, int P>
 __global__ void sample_rows_kernel(GeomParams gp, const int* __restrict__ samp, int ns,
                                    double* __restrict__ sK, double* __restrict__ sM, int* status) {
@@ -148,8 +151,10 @@ __global__ void sample_rows_kernel(GeomParams gp, const int* __restrict__ samp, 
     double* accM = accK + S::DD;              // [DD]
     double* Gq = accM + S::DD;                // [nqd][NS]
     double* wq = Gq + nqd * S::NS;            // [nqd]
-    double* Ga = wq + nqd;                    // [nqd][DIM]   G grad phi_a
-    double* va = Ga + nqd * DIM;              // [nqd]        phi_a wm
+    f2* Ga = reinterpret_cast<f2*>(wq + nqd);   // [nqd][DIM]   G grad phi_a
+    f2* va = Ga + nqd * DIM;                    // [nqd]        phi_a wm
+    const f2* bv2 = reinterpret_cast<const f2*>(gp.bval2);
+    const f2* bd2 = reinterpret_cast<const f2*>(gp.bder2);
 
     int sidx[3] = {0, 0, 0}, row[3] = {0, 0, 0};
     decode<DIM>(blockIdx.x, ns, sidx);
@@ -173,27 +178,40 @@ __global__ void sample_rows_kernel(GeomParams gp, const int* __restrict__ samp, 
             local_basis<DIM, P>(gp, e, g, al, gr, v);
             sym_matvec<DIM>(G, gr, Gg);
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) Ga[q * DIM + k] = Gg[k];
-            va[q] = v * wm;
+            for (int k = 0; k < DIM; ++k) Ga[q * DIM + k] = df_from(Gg[k]);
+            va[q] = df_from(v * wm);
         }
         __syncthreads();
         for (int b = threadIdx.x; b < S::NLOC; b += blockDim.x) {
             int bl[3] = {0, 0, 0};
             decode<DIM>(b, P + 1, bl);
-            double kv = 0.0, mv = 0.0;
+            f2 kv = {0.f, 0.f}, mv = {0.f, 0.f};
             for (int q = 0; q < nqd; ++q) {
                 int g[3] = {0, 0, 0};
                 decode<DIM>(q, nq, g);
-                double gr[DIM], v;
-                local_basis<DIM, P>(gp, e, g, bl, gr, v);
+                f2 v[DIM], dv[DIM];
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) kv += Ga[q * DIM + k] * gr[k];
-                mv += va[q] * v;
+                for (int k = 0; k < DIM; ++k) {
+                    const int ti = (e[k] * nq + g[k]) * (P + 1) + bl[k];
+                    v[k] = bv2[ti];
+                    dv[k] = bd2[ti];
+                }
+                f2 vv = v[0];
+#pragma unroll
+                for (int k = 1; k < DIM; ++k) vv = df_mul(vv, v[k]);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    f2 gk = k == 0 ? dv[0] : v[0];
+#pragma unroll
+                    for (int j = 1; j < DIM; ++j) gk = df_mul(gk, j == k ? dv[j] : v[j]);
+                    df_mac(kv, Ga[q * DIM + k], gk);
+                }
+                df_mac(mv, va[q], vv);
             }
             int t = 0;
             for (int k = DIM - 1; k >= 0; --k) t = t * S::PP + (bl[k] - al[k] + P);
-            accK[t] += kv;   // distinct t for distinct b within one element
-            accM[t] += mv;
+            accK[t] += df_value(kv);   // distinct t for distinct b within one element
+            accM[t] += df_value(mv);
         }
     }
     __syncthreads();
